@@ -1,0 +1,353 @@
+"""Benchmark of the RadiusFPS hot path on GB300: one JSON line on rank 0.
+
+A step is one full pass of the path over one cloud: device-side voxel index
+build (bounding box, binning, sort, records) plus the persistent sampling
+kernel (initial update, then M - 1 select / prune / skip / update / resync
+iterations).  Default workload: the room-like cloud, N = 100,000 points,
+M = 25,000 samples, start 0 (synthetic stand-in for the paper's indoor
+scans).  Other workloads: --workload uniform4k | lidar1m.
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
+on the launching stream; between steps a 256 MiB buffer is written to flush
+the 129 MB L2 (outside the events).  Barrier + synchronize on both sides of
+the timed loop, max over ranks.  Multi-GPU: one process per GPU, each samples
+its own cloud (clouds are independent units; no data-path collective).
+
+--impl reference times the CPU oracle (plain FPS, all host cores) on the
+same workload instead (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "samples/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="room100k", choices=["room100k", "uniform4k", "lidar1m"])
+    ap.add_argument("--opts", default="", help="JSON dict of rfps_opts overrides")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return PEAKS_FALLBACK["hbm_gbs"], "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("rfps_sample.cu", "rfps_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2606_06255_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per launch of the sampling kernel from the committed ncu summary, if current."""
+    p = os.path.join(ROOT, "profiles", f"k_sample_{workload}.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def cpu_threads():
+    import oracle
+    return oracle.openmp_threads() or 1
+
+
+def time_oracle(cloud, budget_s=10.0, max_s=30.0):
+    """The oracle as it stands (plain FPS, every host core) on the full workload, repeated ~10 s."""
+    import oracle
+    reps, t_total = 0, 0.0
+    while t_total < budget_s and reps < 1000:
+        t0 = time.perf_counter()
+        oracle.fps(cloud.points, cloud.m, cloud.start, threads=0)
+        t_total += time.perf_counter() - t0
+        reps += 1
+        if t_total > max_s:
+            break
+    return reps, t_total
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    import cloudgen
+    (cloud,), desc = cloudgen.workload(args.workload, seed=0)
+    threads = cpu_threads()
+    # warm-up, then K timed steps; each step one full oracle run of the workload
+    for _ in range(min(args.warmup, 1)):
+        time_oracle(cloud, budget_s=0.0)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        import oracle
+        oracle.fps(cloud.points, cloud.m, cloud.start, threads=0)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(times)
+    value = cloud.m / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": desc, "n": int(cloud.points.shape[0]), "m": cloud.m},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": threads, "kind": "oracle",
+                         "sample": f"full {args.workload} workload per step (plain FPS oracle, OpenMP)"},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    import torch.distributed as dist
+
+    import cloudgen
+    import paper_2606_06255_gb300 as rf
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    (cloud,), desc = cloudgen.workload(args.workload, seed=rank)
+    n, m, start = cloud.points.shape[0], cloud.m, cloud.start
+    opts = json.loads(args.opts) if args.opts else None
+    pts = torch.from_numpy(cloud.points).to(dev)
+    ws = torch.empty(rf.workspace_size(n, opts), dtype=torch.uint8, device=dev)
+    out = torch.empty(m, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        rf.fps(pts, m, start, opts=opts, workspace=ws, out=out)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if rf.status(ws) != 0:
+        raise RuntimeError("device status after warm-up: %d" % rf.status(ws))
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = rf.launch_count()
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    launches = rf.launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps * m / (total_ms / 1e3)
+
+    # ---- the sampling kernel alone (index path: tiny re-arm kernel + k_sample), for the roofline
+    ix = rf.Index(pts, opts=opts)
+    for _ in range(2):
+        ix.sample(m, start, out=out)
+    sample_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ix.sample(m, start, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sample_ms.append(e0.elapsed_time(e1))
+    ix.free()
+    k_ms = statistics.mean(sample_ms)
+
+    # ---- algorithmic bytes of one sampling launch, from the work counters (untimed run)
+    cws = torch.empty(rf.workspace_size(n, dict(opts or {}, counters=1)), dtype=torch.uint8, device=dev)
+    rf.fps(pts, m, start, opts=dict(opts or {}, counters=1), workspace=cws, out=out)
+    c = rf.counters(cws)
+    resynced = c["voxel_tests"] - c["voxels_pruned"]
+    alg_bytes = 32 * c["voxel_tests"] + 16 * c["points_visited"] + 4 * c["points_updated"] + 8 * resynced
+    peak, peak_kind = load_peaks()
+    achieved = alg_bytes / (k_ms / 1e3) / 1e9
+
+    # ---- plain GPU FPS on the same cloud (best plain variant for the size)
+    plain = None
+    if not args.no_plain:
+        variant = 2 if n > 200000 else 1
+        pws = torch.empty(rf.plain_workspace_size(n), dtype=torch.uint8, device=dev)
+        rf.plain_fps(pts, m, start, variant=variant, workspace=pws, out=out)
+        torch.cuda.synchronize()
+        p_ms = []
+        for _ in range(max(2, min(args.steps, 5))):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rf.plain_fps(pts, m, start, variant=variant, workspace=pws, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            p_ms.append(e0.elapsed_time(e1))
+        pm = statistics.mean(p_ms)
+        plain = {"variant": variant, "ms_per_cloud": pm, "samples_per_s": m / (pm / 1e3),
+                 "radiusfps_speedup": pm / ms_per_step}
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    host_pts = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
+    host_pts.copy_(torch.from_numpy(cloud.points))
+    hws = torch.empty(rf.host_workspace_size(n, opts), dtype=torch.uint8, device=dev)
+    hp = host_pts.numpy()
+    rf.fps_host(hp, m, start, opts=opts, workspace=hws)
+    e2e_s = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rf.fps_host(hp, m, start, opts=opts, workspace=hws)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_value = world * m / statistics.mean(e2e_s)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        reps, secs = time_oracle(cloud)
+        cpu = {"value": reps * m / secs, "unit": "samples/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"{reps} full run(s) of the {args.workload} workload (N={n}, M={m}), "
+                         f"plain FPS oracle with OpenMP, {secs:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": desc, "n": n, "m": m, "start": start,
+                       "clouds_per_gpu_per_step": 1, "l2": "flushed between steps (256 MiB write)",
+                       "opts": opts or "default"},
+            "ms_per_cloud": ms_per_step,
+            "plain_gpu_fps": plain,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": ncu_traffic(args.workload),
+                         "kernel": "k_sample", "kernel_ms": k_ms, "alg_bytes_per_launch": alg_bytes,
+                         "peak_kind": peak_kind,
+                         "ns_per_iteration": k_ms * 1e6 / max(1, m - 1)},
+            "counters": c,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": n * 12,
+                    "d2h_bytes_per_step": m * 8},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,234 @@
+/*
+ * rfps.h -- C ABI of the GB300 (sm_103a) RadiusFPS library (librfps.so).
+ *
+ * Exact farthest point sampling (FPS) accelerated by spherical-voxel
+ * pruning, after "RadiusFPS" (Sec. 3 and Sec. 4 of the paper).  Given a cloud
+ * P = {p_0 .. p_{N-1}} in R^3, a sample count M and a start index, the
+ * library returns the M indices that plain FPS (Alg. 1) selects, in
+ * selection order, in the original indexing of P (Sec. 3.1, Notation).
+ *
+ * Arithmetic contract (identical results on every path of this library):
+ *   - distances are FP32 squared distances (dx*dx + dy*dy) + dz*dz with
+ *     dx = p.x - q.x etc., each operation rounded to nearest, no fused
+ *     multiply-add, no flush-to-zero;
+ *   - each point keeps its FP32 squared distance to the nearest sample and
+ *     replaces it only by a strictly smaller value;
+ *   - argmax ties go to the smallest original index (Sec. 3.1).
+ * The voxel pruning (Sec. 3.4.2) and the point skip (Sec. 3.4.3) are
+ * conservative in this arithmetic, so the RadiusFPS path returns exactly the
+ * plain-FPS indices.
+ *
+ * Conventions for every call:
+ *   - "device" pointers are CUDA global-memory addresses on the current
+ *     device; "host" pointers are ordinary CPU memory;
+ *   - points are an array of N x 3 float32 in (x, y, z) order, row-major
+ *     (array of structures), 4-byte aligned; the library only reads them;
+ *   - output indices are int64 in original (per-cloud) indexing;
+ *   - the caller owns every buffer it passes; the library never frees or
+ *     keeps a caller buffer beyond the call (rfps_index_* keeps its own copy);
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); device work is enqueued on it asynchronously unless a call
+ *     says it synchronises;
+ *   - a call that returns RFPS_OK has enqueued its work.  Argument errors are
+ *     found on the host before anything is enqueued.  Errors only the device
+ *     can see (a non-finite coordinate, an invalid per-cloud entry of a
+ *     device array) are written to a status word in the workspace and read
+ *     back with rfps_status_read();
+ *   - no call traps, asserts on the device or waits without a bound.
+ */
+#ifndef RFPS_H
+#define RFPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum {
+    RFPS_OK = 0,
+    RFPS_EINVAL = 1,      /* invalid argument (host check, or device check of a device array) */
+    RFPS_ENONFINITE = 2,  /* a coordinate is NaN or +-inf (found on the device) */
+    RFPS_ENOMEM = 3,      /* workspace too small, or a device allocation failed */
+    RFPS_ECUDA = 4,       /* a CUDA runtime call failed */
+    RFPS_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
+    RFPS_EUNSUPPORTED = 6 /* no sm_103a device, or a launch shape the device cannot run */
+} rfps_status;
+
+/* Tuning knobs.  Zero means "choose automatically" for every field but the
+ * three switches, whose defaults (from rfps_opts_default) are 1, 1, 0. */
+typedef struct {
+    int32_t n_vox;       /* voxel bins per axis, n_vox of Sec. 3.2 (v in Sec. 5.6.2); 1..256 */
+    int32_t cluster;     /* CTAs working on one cloud (thread-block cluster size): 1,2,4,8,16 */
+    int32_t threads;     /* threads per CTA of the sampling kernel: 256, 512 or 1024 */
+    int32_t chunk;       /* max points per voxel record (a voxel with more points is split
+                            into several records): power of two in 32..4096 */
+    int32_t prune;       /* 1: spherical-voxel radius pruning (Sec. 3.4.2) on */
+    int32_t skip;        /* 1: coordinate-wise point skip (Sec. 3.4.3) on */
+    int32_t radius_mode; /* 0: radius measured over the members (tighter, default);
+                            1: the paper's sqrt(3)/2 * L (Eq. preprocess_voxel_radius),
+                               raised to the measured value if rounding requires it */
+    int32_t counters;    /* 1: accumulate work counters (rfps_counters_read); slower */
+} rfps_opts;
+
+/* Work counters of the sampling loop (Fig. samplestep / Tab. ablation
+ * statistics), summed over all iterations and clouds of one call. */
+typedef struct {
+    uint64_t voxel_tests;     /* voxel-record prune tests */
+    uint64_t voxels_pruned;   /* records skipped by Eq. radius_pruning_condition */
+    uint64_t points_visited;  /* points of unpruned records */
+    uint64_t points_skipped;  /* points dropped by Eq. point_skip_condition */
+    uint64_t points_updated;  /* strict decreases of a stored distance (effective updates) */
+    uint64_t iterations;      /* sampling iterations (selections after the start point) */
+} rfps_counters;
+
+/* Fills *opts with the defaults (all automatic, prune = skip = 1). */
+void rfps_opts_default(rfps_opts *opts);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *rfps_status_str(int status);
+
+/* Library ABI version (increments when a signature or struct changes). */
+int rfps_version(void);
+
+/* Total kernels this process has launched through the library so far. */
+int64_t rfps_launch_count(void);
+
+/* ------------------------------------------------------------------------
+ * Single cloud.
+ *
+ * rfps_fps: M samples of one cloud with RadiusFPS (Sec. 3, Sec. 4): the
+ * device builds the spherical-voxel index (bounding box, Eq. voxel_size,
+ * binning, active voxels with centre and radius -- Sec. 3.2, Alg.
+ * voxelization_gpu), runs the initial update from `start` (Sec. 3.3), then
+ * M - 1 iterations of select / radius prune / point skip / update / voxel
+ * resync (Sec. 3.4) in one persistent kernel.
+ *   points     device, N x 3 float32
+ *   n          N >= 1, N < 2^31
+ *   m          1 <= M <= N
+ *   start      0 <= start < N (the paper draws it uniformly, Sec. 3.3; here the
+ *              caller chooses it)
+ *   out_idx    device, M int64, receives the indices; out_idx[0] = start
+ *   opts       NULL for defaults
+ *   workspace  device scratch of at least rfps_fps_workspace_size() bytes,
+ *              256-byte aligned, owned by the caller, not read before the call
+ *              (its status word is valid until the next call that uses it)
+ * Errors: RFPS_EINVAL (bad argument, nothing enqueued), RFPS_ENOMEM
+ * (workspace too small), RFPS_EUNSUPPORTED, RFPS_ECUDA; a non-finite
+ * coordinate is reported by rfps_status_read() as RFPS_ENONFINITE and then
+ * out_idx is left unspecified.
+ * ---------------------------------------------------------------------- */
+size_t rfps_fps_workspace_size(int64_t n, const rfps_opts *opts);
+rfps_status rfps_fps(const float *points, int64_t n, int64_t m, int64_t start,
+                     int64_t *out_idx, const rfps_opts *opts, void *workspace,
+                     size_t workspace_bytes, void *stream);
+
+/* rfps_fps_host: the same call on HOST buffers.  Copies the points into the
+ * workspace (which must hold rfps_fps_host_workspace_size() bytes), samples,
+ * copies the indices back to host_out, and synchronises `stream`.  Returns
+ * the device status (so RFPS_ENONFINITE is reported directly). */
+size_t rfps_fps_host_workspace_size(int64_t n, const rfps_opts *opts);
+rfps_status rfps_fps_host(const float *host_points, int64_t n, int64_t m,
+                          int64_t start, int64_t *host_out, const rfps_opts *opts,
+                          void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Ragged batch: B clouds concatenated in one point array, sampled by one
+ * persistent launch whose CTA clusters take clouds from a device work queue
+ * (largest clouds first).
+ *   points       device, total_n x 3 float32 (cloud b = rows offsets[b] ..
+ *                offsets[b+1]-1)
+ *   offsets      device int64[B+1], offsets[0] = 0, non-decreasing,
+ *                offsets[B] = total_n, every cloud non-empty
+ *   out_offsets  device int64[B+1]: cloud b writes M_b = out_offsets[b+1] -
+ *                out_offsets[b] indices at out_idx + out_offsets[b];
+ *                1 <= M_b <= N_b
+ *   starts       device int64[B], start index of each cloud in its own indexing
+ *   max_n        host-known upper bound on every N_b (sizes the launch)
+ *   out_idx      device int64[out_offsets[B]], per-cloud (local) indices
+ * Device-detected violations of the array contracts set RFPS_EINVAL in the
+ * status word and skip the offending cloud.
+ * ---------------------------------------------------------------------- */
+size_t rfps_batch_workspace_size(int64_t total_n, int64_t b, int64_t max_n,
+                                 const rfps_opts *opts);
+rfps_status rfps_fps_batched(const float *points, int64_t total_n,
+                             const int64_t *offsets, int64_t b,
+                             const int64_t *out_offsets, const int64_t *starts,
+                             int64_t max_n, int64_t *out_idx,
+                             const rfps_opts *opts, void *workspace,
+                             size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Plain O(N*M) GPU FPS (Alg. 1), the comparison baseline, same arithmetic
+ * and tie rule.
+ *   variant 0: one CTA per cloud streaming the cloud every iteration (the
+ *              classic FPS kernel design);
+ *   variant 1: one thread-block cluster per cloud with the cloud resident in
+ *              the cluster's shared memory when it fits, else streamed from L2;
+ *   variant 2: the whole GPU on one cloud: one CTA per SM, each holding a
+ *              slice of the cloud in shared memory, with a bounded
+ *              software grid barrier per iteration (single cloud only).
+ * Batched form: same array contracts as rfps_fps_batched (variants 0 and 1).
+ * ---------------------------------------------------------------------- */
+size_t rfps_plain_workspace_size(int64_t total_n, int64_t b);
+rfps_status rfps_plain_fps(const float *points, int64_t n, int64_t m,
+                           int64_t start, int64_t *out_idx, int32_t variant,
+                           void *workspace, size_t workspace_bytes, void *stream);
+rfps_status rfps_plain_fps_batched(const float *points, int64_t total_n,
+                                   const int64_t *offsets, int64_t b,
+                                   const int64_t *out_offsets,
+                                   const int64_t *starts, int64_t max_n,
+                                   int64_t *out_idx, int32_t variant,
+                                   void *workspace, size_t workspace_bytes,
+                                   void *stream);
+
+/* ------------------------------------------------------------------------
+ * Device status and counters of a workspace.  Both synchronise `stream`.
+ * rfps_status_read returns the first error the device recorded for the last
+ * call that used `workspace` (RFPS_OK if none).
+ * rfps_counters_read fills *out with the counters of the last call that ran
+ * with opts.counters = 1 (zeros otherwise).
+ * ---------------------------------------------------------------------- */
+rfps_status rfps_status_read(const void *workspace, void *stream);
+rfps_status rfps_counters_read(const void *workspace, rfps_counters *out,
+                               void *stream);
+
+/* ------------------------------------------------------------------------
+ * Persistent index for serving: the spherical-voxel index (Sec. 3.2) of one
+ * cloud is built once, kept on the device in library-owned memory, and
+ * sampled any number of times with different M / start.
+ *   rfps_index_build   copies nothing from the caller after it returns: the
+ *                      index holds the sorted points it needs.  Allocates
+ *                      device memory (cudaMallocAsync on `stream`).
+ *   rfps_index_sample  M samples from the index (same contract as rfps_fps).
+ *   rfps_index_bytes   device bytes the index holds.
+ *   rfps_index_free    releases the index (stream-ordered on the stream it was
+ *                      built on); NULL is ignored.
+ *   rfps_index_export  copies the voxel records to HOST arrays for inspection
+ *                      (synchronises): per record its voxel id (v_z n^2 + v_y n
+ *                      + v_x), first sorted position, point count, centre and
+ *                      radius (float4 each), plus each sorted position's
+ *                      original index.  Pass NULL for arrays not wanted;
+ *                      *n_records receives the record count.
+ * ---------------------------------------------------------------------- */
+typedef struct rfps_index rfps_index;
+rfps_status rfps_index_build(const float *points, int64_t n,
+                             const rfps_opts *opts, rfps_index **out,
+                             void *stream);
+rfps_status rfps_index_sample(rfps_index *index, int64_t m, int64_t start,
+                              int64_t *out_idx, void *stream);
+size_t rfps_index_bytes(const rfps_index *index);
+void rfps_index_free(rfps_index *index);
+rfps_status rfps_index_export(const rfps_index *index, int64_t *n_records,
+                              uint32_t *voxel_id, uint32_t *first,
+                              uint32_t *count, float *sphere4,
+                              uint32_t *sorted_orig, float *grid4,
+                              int32_t *n_vox);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RFPS_H */

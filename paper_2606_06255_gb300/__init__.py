@@ -1,0 +1,26 @@
+"""GB300-native RadiusFPS: exact farthest point sampling with spherical-voxel pruning.
+
+The compute path is librfps.so (hand-written sm_103a CUDA behind the C ABI of
+include/rfps.h); this package is its thin Python binding plus the batching,
+autotuning and serving layers around it.
+"""
+
+from ._lib import (  # noqa: F401
+    Counters,
+    Index,
+    Opts,
+    RfpsError,
+    batch_workspace_size,
+    counters,
+    fps,
+    fps_batched,
+    fps_host,
+    host_workspace_size,
+    launch_count,
+    lib,
+    plain_fps,
+    plain_fps_batched,
+    plain_workspace_size,
+    status,
+    workspace_size,
+)

@@ -1,0 +1,308 @@
+"""ctypes binding of librfps.so (the C ABI in include/rfps.h).
+
+Argument marshalling only: every step of sampling runs in the library's CUDA
+kernels.  PyTorch provides device memory and the current stream.  There is no
+CPU fallback: if librfps.so is missing or cannot be loaded, importing this
+module raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librfps.so")
+
+OK, EINVAL, ENONFINITE, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(7)
+
+
+class RfpsError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        super().__init__(f"{what}: {_lib.rfps_status_str(int(status)).decode()} (status {int(status)})")
+
+
+class Opts(ctypes.Structure):
+    """rfps_opts: zero = automatic, except prune / skip (default 1)."""
+    _fields_ = [("n_vox", ctypes.c_int32), ("cluster", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("chunk", ctypes.c_int32), ("prune", ctypes.c_int32), ("skip", ctypes.c_int32),
+                ("radius_mode", ctypes.c_int32), ("counters", ctypes.c_int32)]
+
+    def __init__(self, **kw):
+        super().__init__()
+        _lib.rfps_opts_default(ctypes.byref(self))
+        for k, v in kw.items():
+            if k not in {f[0] for f in self._fields_}:
+                raise TypeError(f"unknown option {k}")
+            setattr(self, k, int(v))
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
+
+
+class Counters(ctypes.Structure):
+    _fields_ = [("voxel_tests", ctypes.c_uint64), ("voxels_pruned", ctypes.c_uint64),
+                ("points_visited", ctypes.c_uint64), ("points_skipped", ctypes.c_uint64),
+                ("points_updated", ctypes.c_uint64), ("iterations", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f[0]: int(getattr(self, f[0])) for f in self._fields_}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; g.build()\"`"
+                          " (or python paper_2606_06255_gb300/build.py)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, sz, i64, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64, ctypes.c_int32
+    optp = ctypes.POINTER(Opts)
+    st = ctypes.c_int
+    sig = {
+        "rfps_opts_default": (None, [optp]),
+        "rfps_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+        "rfps_version": (ctypes.c_int, []),
+        "rfps_launch_count": (i64, []),
+        "rfps_fps_workspace_size": (sz, [i64, optp]),
+        "rfps_fps": (st, [vp, i64, i64, i64, vp, optp, vp, sz, vp]),
+        "rfps_fps_host_workspace_size": (sz, [i64, optp]),
+        "rfps_fps_host": (st, [vp, i64, i64, i64, vp, optp, vp, sz, vp]),
+        "rfps_batch_workspace_size": (sz, [i64, i64, i64, optp]),
+        "rfps_fps_batched": (st, [vp, i64, vp, i64, vp, vp, i64, vp, optp, vp, sz, vp]),
+        "rfps_plain_workspace_size": (sz, [i64, i64]),
+        "rfps_plain_fps": (st, [vp, i64, i64, i64, vp, i32, vp, sz, vp]),
+        "rfps_plain_fps_batched": (st, [vp, i64, vp, i64, vp, vp, i64, vp, i32, vp, sz, vp]),
+        "rfps_status_read": (st, [vp, vp]),
+        "rfps_counters_read": (st, [vp, ctypes.POINTER(Counters), vp]),
+        "rfps_index_build": (st, [vp, i64, optp, ctypes.POINTER(vp), vp]),
+        "rfps_index_sample": (st, [vp, i64, i64, vp, vp]),
+        "rfps_index_bytes": (sz, [vp]),
+        "rfps_index_free": (None, [vp]),
+        "rfps_index_export": (st, [vp, ctypes.POINTER(i64), vp, vp, vp, vp, vp, vp, ctypes.POINTER(i32)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        raise RfpsError(status, what)
+
+
+def _opts(opts):
+    if opts is None:
+        return None
+    if isinstance(opts, Opts):
+        return ctypes.byref(opts)
+    return ctypes.byref(Opts(**opts))
+
+
+def _points(points: torch.Tensor) -> torch.Tensor:
+    if not isinstance(points, torch.Tensor) or not points.is_cuda:
+        raise TypeError("points must be a CUDA tensor of shape (N, 3)")
+    if points.dtype != torch.float32 or points.dim() != 2 or points.shape[1] != 3:
+        raise TypeError("points must be float32 with shape (N, 3)")
+    return points.contiguous()
+
+
+def _workspace(nbytes: int, device, workspace=None) -> torch.Tensor:
+    if nbytes == 0:
+        raise RfpsError(EINVAL, "workspace size")
+    if workspace is not None:
+        if workspace.numel() * workspace.element_size() < nbytes or workspace.data_ptr() % 256:
+            raise RfpsError(ENOMEM, "workspace")
+        return workspace
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def workspace_size(n: int, opts=None) -> int:
+    return int(_lib.rfps_fps_workspace_size(n, _opts(opts)))
+
+
+def fps(points: torch.Tensor, m: int, start: int = 0, opts=None, workspace=None, stream=None,
+        out: torch.Tensor | None = None, check: bool = False):
+    """RadiusFPS: int64 indices (M,) of the samples, on the points' device.
+
+    check=True synchronises and raises on a device-side error (e.g. a
+    non-finite coordinate); otherwise the call is asynchronous.
+    """
+    p = _points(points)
+    n = p.shape[0]
+    ws = _workspace(workspace_size(n, opts), p.device, workspace)
+    if out is None:
+        out = torch.empty(m, dtype=torch.int64, device=p.device)
+    s = _stream(stream)
+    _check(_lib.rfps_fps(p.data_ptr(), n, m, start, out.data_ptr(), _opts(opts), ws.data_ptr(),
+                         ws.numel(), s), "rfps_fps")
+    if check:
+        _check(_lib.rfps_status_read(ws.data_ptr(), s), "rfps_fps (device)")
+    return out
+
+
+def fps_host(points: np.ndarray, m: int, start: int = 0, opts=None, workspace=None, stream=None) -> np.ndarray:
+    """RadiusFPS on host buffers (copies in and out inside the call, synchronises)."""
+    p = np.ascontiguousarray(points, dtype=np.float32)
+    if p.ndim != 2 or p.shape[1] != 3:
+        raise TypeError("points must have shape (N, 3)")
+    n = p.shape[0]
+    nbytes = int(_lib.rfps_fps_host_workspace_size(n, _opts(opts)))
+    ws = _workspace(nbytes, torch.device("cuda", torch.cuda.current_device()), workspace)
+    out = np.empty(m, dtype=np.int64)
+    _check(_lib.rfps_fps_host(p.ctypes.data, n, m, start, out.ctypes.data, _opts(opts), ws.data_ptr(), ws.numel(),
+                              _stream(stream)), "rfps_fps_host")
+    return out
+
+
+def host_workspace_size(n: int, opts=None) -> int:
+    return int(_lib.rfps_fps_host_workspace_size(n, _opts(opts)))
+
+
+def _batch_meta(sizes, ms, starts, device):
+    sizes = [int(x) for x in sizes]
+    ms = [int(x) for x in ms]
+    starts = [int(x) for x in (starts if starts is not None else [0] * len(sizes))]
+    off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)
+    ooff = np.zeros(len(sizes) + 1, dtype=np.int64)
+    ooff[1:] = np.cumsum(ms)
+    t = lambda a: torch.from_numpy(a).to(device)
+    return t(off), t(ooff), t(np.array(starts, dtype=np.int64)), off, ooff, max(sizes)
+
+
+def batch_workspace_size(total_n: int, b: int, max_n: int, opts=None) -> int:
+    return int(_lib.rfps_batch_workspace_size(total_n, b, max_n, _opts(opts)))
+
+
+def fps_batched(points: torch.Tensor, sizes, ms, starts=None, opts=None, workspace=None, stream=None, meta=None):
+    """Ragged batch in one launch: returns (indices concatenated, host out-offsets)."""
+    p = _points(points)
+    if meta is None:
+        meta = _batch_meta(sizes, ms, starts, p.device)
+    d_off, d_ooff, d_st, off, ooff, max_n = meta
+    b = len(off) - 1
+    ws = _workspace(batch_workspace_size(p.shape[0], b, max_n, opts), p.device, workspace)
+    out = torch.empty(int(ooff[-1]), dtype=torch.int64, device=p.device)
+    _check(_lib.rfps_fps_batched(p.data_ptr(), p.shape[0], d_off.data_ptr(), b, d_ooff.data_ptr(), d_st.data_ptr(),
+                                 max_n, out.data_ptr(), _opts(opts), ws.data_ptr(), ws.numel(), _stream(stream)),
+           "rfps_fps_batched")
+    return out, ooff
+
+
+def plain_workspace_size(total_n: int, b: int = 1) -> int:
+    return int(_lib.rfps_plain_workspace_size(total_n, b))
+
+
+def plain_fps(points: torch.Tensor, m: int, start: int = 0, variant: int = 1, workspace=None, stream=None,
+              out: torch.Tensor | None = None):
+    """Plain O(N*M) GPU FPS baseline (variant 0 classic, 1 cluster, 2 whole GPU)."""
+    p = _points(points)
+    n = p.shape[0]
+    ws = _workspace(plain_workspace_size(n), p.device, workspace)
+    if out is None:
+        out = torch.empty(m, dtype=torch.int64, device=p.device)
+    _check(_lib.rfps_plain_fps(p.data_ptr(), n, m, start, out.data_ptr(), variant, ws.data_ptr(), ws.numel(),
+                               _stream(stream)), "rfps_plain_fps")
+    return out
+
+
+def plain_fps_batched(points: torch.Tensor, sizes, ms, starts=None, variant: int = 1, workspace=None, stream=None,
+                      meta=None):
+    p = _points(points)
+    if meta is None:
+        meta = _batch_meta(sizes, ms, starts, p.device)
+    d_off, d_ooff, d_st, off, ooff, max_n = meta
+    b = len(off) - 1
+    ws = _workspace(plain_workspace_size(p.shape[0], b), p.device, workspace)
+    out = torch.empty(int(ooff[-1]), dtype=torch.int64, device=p.device)
+    _check(_lib.rfps_plain_fps_batched(p.data_ptr(), p.shape[0], d_off.data_ptr(), b, d_ooff.data_ptr(),
+                                       d_st.data_ptr(), max_n, out.data_ptr(), variant, ws.data_ptr(), ws.numel(),
+                                       _stream(stream)), "rfps_plain_fps_batched")
+    return out, ooff
+
+
+def status(workspace: torch.Tensor, stream=None) -> int:
+    return int(_lib.rfps_status_read(workspace.data_ptr(), _stream(stream)))
+
+
+def counters(workspace: torch.Tensor, stream=None) -> dict:
+    c = Counters()
+    _check(_lib.rfps_counters_read(workspace.data_ptr(), ctypes.byref(c), _stream(stream)), "rfps_counters_read")
+    return c.as_dict()
+
+
+def launch_count() -> int:
+    return int(_lib.rfps_launch_count())
+
+
+class Index:
+    """Device-resident spherical-voxel index of one cloud (rfps_index_*)."""
+
+    def __init__(self, points: torch.Tensor, opts=None, stream=None):
+        p = _points(points)
+        self.n = p.shape[0]
+        self.device = p.device
+        h = ctypes.c_void_p()
+        _check(_lib.rfps_index_build(p.data_ptr(), self.n, _opts(opts), ctypes.byref(h), _stream(stream)),
+               "rfps_index_build")
+        self._h = h
+
+    @property
+    def nbytes(self) -> int:
+        return int(_lib.rfps_index_bytes(self._h))
+
+    def sample(self, m: int, start: int = 0, stream=None, out: torch.Tensor | None = None) -> torch.Tensor:
+        if self._h is None:
+            raise RuntimeError("index freed")
+        if out is None:
+            out = torch.empty(m, dtype=torch.int64, device=self.device)
+        _check(_lib.rfps_index_sample(self._h, m, start, out.data_ptr(), _stream(stream)), "rfps_index_sample")
+        return out
+
+    def export(self) -> dict:
+        n = self.n
+        R = ctypes.c_int64()
+        _check(_lib.rfps_index_export(self._h, ctypes.byref(R), None, None, None, None, None, None, None),
+               "rfps_index_export")
+        r = R.value
+        vid = np.empty(r, np.uint32)
+        first = np.empty(r, np.uint32)
+        cnt = np.empty(r, np.uint32)
+        sph = np.empty((r, 4), np.float32)
+        orig = np.empty(n, np.uint32)
+        grid = np.empty(4, np.float32)
+        nv = ctypes.c_int32()
+        _check(_lib.rfps_index_export(self._h, ctypes.byref(R), vid.ctypes.data, first.ctypes.data, cnt.ctypes.data,
+                                      sph.ctypes.data, orig.ctypes.data, grid.ctypes.data, ctypes.byref(nv)),
+               "rfps_index_export")
+        return {"voxel_id": vid, "first": first, "count": cnt, "sphere": sph, "sorted_orig": orig,
+                "grid_min": grid[:3].copy(), "L": np.float32(grid[3]), "n_vox": nv.value}
+
+    def free(self):
+        if self._h is not None:
+            _lib.rfps_index_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -1,0 +1,175 @@
+// rfps_common.cuh -- device arithmetic shared by the sampling kernels.
+//
+// Every floating-point step below uses the explicitly rounded intrinsics
+// (__fsub_rn, __fmul_rn, __fadd_rn, __fsqrt_rn) so that nvcc can neither
+// contract a multiply and an add into an FMA nor reassociate: the squared
+// distance is exactly (dx*dx + dy*dy) + dz*dz in FP32 round-to-nearest, the
+// canonical arithmetic of the library (reading of Sec. 3.1: "same
+// floating-point precision").  The library is built without --use_fast_math
+// and without flush-to-zero.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rfps {
+
+constexpr uint32_t kStatusOk = 0;
+constexpr uint32_t kStatusInval = 1;
+constexpr uint32_t kStatusNonFinite = 2;
+constexpr uint32_t kStatusTimeout = 5;
+
+// Canonical FP32 squared distance between p and s.
+__device__ __forceinline__ float sq_dist(float px, float py, float pz, float sx, float sy, float sz)
+{
+    const float dx = __fsub_rn(px, sx);
+    const float dy = __fsub_rn(py, sy);
+    const float dz = __fsub_rn(pz, sz);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// Argmax key of a point: (bits of its squared distance) << 32 | ~index.
+// Stored distances are >= +0 (never -0: a difference of equal floats is +0
+// and squares are non-negative), so the IEEE bit pattern orders like the
+// value, +inf included.  The low word ~index makes the larger key the one
+// with the smaller index on equal distances: max over keys is the argmax
+// with the smallest-original-index tie rule of Sec. 3.1, and the same
+// max-of-keys over a voxel is its Dist_v (Eq. preprocess_distv) together
+// with the index that attains it (the tie-exact two-level selection of
+// Eq. global_equivalent_selection).
+__device__ __forceinline__ unsigned long long make_key(float d2, uint32_t index)
+{
+    return (static_cast<unsigned long long>(__float_as_uint(d2)) << 32) | static_cast<unsigned long long>(~index);
+}
+__device__ __forceinline__ float key_d2(unsigned long long key) { return __uint_as_float(static_cast<uint32_t>(key >> 32)); }
+__device__ __forceinline__ uint32_t key_index(unsigned long long key) { return ~static_cast<uint32_t>(key); }
+
+// Spherical-voxel radius pruning (Sec. 3.4.2: Eq. spherical_voxel_bound,
+// radius_pruning_condition), decided in FP32 with margins so that it is
+// safe for the FP32 squared distances it protects.  Returns true only if no
+// point of the record can get a strictly smaller stored distance from s.
+//
+// sph = (c_x, c_y, c_z, r): record centre and a radius with r >= |p - c| for
+// every member p (exact reals; guaranteed by the build, see record_radius).
+// key = the record's Dist_v key (max over its points).  u = 2^-24.
+//
+//   dc  = sqrt(fl d2(s, c))              <= (1+u)^3.5 |s - c| + 2^-74
+//   a   = fl(dc * (1 - 2^-20))           <= (1 - 11u) |s - c| + 2^-73
+//   lb  = fl(a - r)                      <= |s - c| - r_true  whenever
+//                                           lb^2 >= 2^-100 (then |s-c| >= 2^-51
+//                                           and the 10u|s-c| slack covers the
+//                                           subtraction's rounding and 2^-73)
+//   so |s - p| >= |s - c| - |p - c| >= lb for every member p, and
+//   fl d2(p, s) >= (1 - 5u) |s - p|^2 - 3 * 2^-150 >= (1 - 5u) lb^2 - 2^-148.
+//   test: t = fl(fl(lb*lb) * (1 - 2^-20)) <= (1 - 13u) lb^2.
+//   For lb^2 >= 2^-100 the 8u lb^2 gap exceeds 2^-148, hence
+//   fl d2(p, s) >= t >= Dist_v >= stored d2(p): the strict update cannot fire.
+// A record whose Dist_v is 0 cannot change either.  Non-finite lb^2 (huge
+// coordinates) never prunes.
+__device__ __forceinline__ bool prune_record(float4 sph, unsigned long long key, float sx, float sy, float sz)
+{
+    const float dv = key_d2(key);
+    if (dv == 0.0f) return true;
+    const float dc = __fsqrt_rn(sq_dist(sx, sy, sz, sph.x, sph.y, sph.z));
+    const float a = __fmul_rn(dc, 0x1.ffffep-1f);          // 1 - 2^-20
+    const float lb = __fsub_rn(a, sph.w);
+    if (!(lb > 0.0f)) return false;
+    const float lb2 = __fmul_rn(lb, lb);
+    if (!(lb2 >= 0x1p-100f) || !(lb2 <= 3.4028234e38f)) return false;
+    return __fmul_rn(lb2, 0x1.ffffep-1f) >= dv;
+}
+
+// Coordinate-wise point skip (Sec. 3.4.3, Eq. point_skip_condition) in the
+// squared domain: skip iff fl(da*da) >= stored d2 for some axis, with the
+// same rounded terms that make up d2.  Adding non-negative floats under
+// round-to-nearest never decreases, so d2 >= fl(da*da) >= stored d2 and the
+// strict update could not fire: the skip is exact, not just conservative.
+__device__ __forceinline__ bool skip_point(float xx, float yy, float zz, float d2old)
+{
+    return xx >= d2old || yy >= d2old || zz >= d2old;
+}
+
+// ---------------------------------------------------------------------------
+// Warp helpers
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
+{
+    uint32_t hi = static_cast<uint32_t>(v >> 32);
+    const uint32_t mhi = __reduce_max_sync(0xffffffffu, hi);
+    uint32_t lo = (hi == mhi) ? static_cast<uint32_t>(v) : 0u;
+    const uint32_t mlo = __reduce_max_sync(0xffffffffu, lo);
+    return (static_cast<unsigned long long>(mhi) << 32) | mlo;
+}
+
+// Lane holding the warp-wide maximum key (keys are unique per point; for
+// equal keys the lowest lane).
+__device__ __forceinline__ int warp_argmax_lane(unsigned long long v, unsigned long long* vmax)
+{
+    const unsigned long long m = warp_max_u64(v);
+    *vmax = m;
+    const uint32_t b = __ballot_sync(0xffffffffu, v == m);
+    return __ffs(b) - 1;
+}
+
+// ---------------------------------------------------------------------------
+// Thread-block cluster helpers (sm_90+ PTX).
+__device__ __forceinline__ uint32_t cluster_ctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_nctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_count_x()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// Full cluster barrier: release my prior shared::cluster writes, acquire the others'.
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Address of `p` (my shared memory) in the shared memory of cluster CTA `rank`.
+__device__ __forceinline__ uint32_t map_shared(const void* p, uint32_t rank)
+{
+    const uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+    return remote;
+}
+__device__ __forceinline__ void st_cluster_u64(uint32_t addr, unsigned long long v)
+{
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster_f32x4(uint32_t addr, float4 v)
+{
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+// Order-preserving float <-> uint encoding for atomic min/max of floats.
+__device__ __forceinline__ uint32_t float_to_ordered(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ordered_to_float(uint32_t u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+}  // namespace rfps

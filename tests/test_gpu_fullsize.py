@@ -1,0 +1,47 @@
+"""Full-size workloads on the GPU vs the OpenMP CPU oracle, index for index.
+
+Sizes are those of the benchmark configurations: the room-like cloud
+(N = 100,000, M = 25,000), the accumulated LiDAR scan (N = 1,124,730,
+M = 16,384), and the ragged 64-cloud batch (M = N/4 each), all through the
+default launch configuration that bench.py times.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import cloudgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rf():
+    import paper_2606_06255_gb300 as rf
+    return rf
+
+
+@pytest.mark.parametrize("name", ["room100k", "lidar1m"])
+def test_single_cloud_full_size(rf, name):
+    (cloud,), _ = cloudgen.workload(name)
+    ref = oracle.fps(cloud.points, cloud.m, cloud.start, threads=0)
+    d = torch.from_numpy(cloud.points).cuda()
+    got = rf.fps(d, cloud.m, cloud.start, check=True).cpu().numpy()
+    np.testing.assert_array_equal(got, ref)
+    # the best plain baseline on the same cloud
+    variant = 2 if cloud.points.shape[0] > 200000 else 1
+    plain = rf.plain_fps(d, cloud.m, cloud.start, variant=variant).cpu().numpy()
+    np.testing.assert_array_equal(plain, ref)
+
+
+def test_batch64_full_size(rf):
+    clouds, _ = cloudgen.workload("batch64")
+    sizes = [c.points.shape[0] for c in clouds]
+    ms = [c.m for c in clouds]
+    cat = torch.from_numpy(np.concatenate([c.points for c in clouds])).cuda()
+    out, ooff = rf.fps_batched(cat, sizes, ms, [0] * len(clouds))
+    out = out.cpu().numpy()
+    for b, c in enumerate(clouds):
+        ref = oracle.fps(c.points, c.m, 0, threads=0)
+        np.testing.assert_array_equal(out[ooff[b]:ooff[b + 1]], ref, err_msg=f"cloud {b} (N={sizes[b]})")

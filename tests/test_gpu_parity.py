@@ -1,0 +1,243 @@
+"""CUDA path vs the CPU oracle, element by element (needs a GB300).
+
+Sample indices are integers decided by FP32 comparisons that both sides make
+in the same precision, so the bar is bit-exact equality of every index.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import cloudgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rf():
+    import paper_2606_06255_gb300 as rf
+    return rf
+
+
+def dev(p):
+    return torch.from_numpy(np.ascontiguousarray(p, dtype=np.float32)).cuda()
+
+
+def gpu_fps(rf, pts, m, start=0, **opts):
+    out = rf.fps(dev(pts), m, start, opts=opts or None, check=True)
+    return out.cpu().numpy()
+
+
+SMALL_CLOUDS = [
+    ("uniform_4096", lambda: cloudgen.uniform_cloud(4096, seed=0), 1024, 0),
+    ("uniform_ragged_5003", lambda: cloudgen.uniform_cloud(5003, seed=1), 1301, 17),
+    ("room_20000", lambda: cloudgen.room_cloud(20000, seed=2), 5000, 0),
+    ("lidar_30001", lambda: cloudgen.lidar_cloud(30001, seed=3), 3000, 123),
+    ("grid_ties", lambda: np.array(np.meshgrid(*[np.arange(16)] * 3), dtype=np.float32).reshape(3, -1).T.copy(),
+     1500, 0),
+]
+
+
+@pytest.mark.parametrize("name,make,m,start", SMALL_CLOUDS, ids=[c[0] for c in SMALL_CLOUDS])
+def test_default_path_matches_oracle(rf, name, make, m, start):
+    pts = make()
+    ref = oracle.fps(pts, m, start, threads=0)
+    np.testing.assert_array_equal(gpu_fps(rf, pts, m, start), ref)
+
+
+OPT_GRID = [
+    dict(cluster=1, threads=256, chunk=32, n_vox=4),
+    dict(cluster=1, threads=1024, chunk=4096, n_vox=64),
+    dict(cluster=2, threads=512, chunk=64, n_vox=16),
+    dict(cluster=4, threads=256, chunk=256, n_vox=32),
+    dict(cluster=8, threads=1024, chunk=128, n_vox=8),
+    dict(cluster=16, threads=512, chunk=512, n_vox=48),
+    dict(cluster=4, threads=512, chunk=256, n_vox=24, prune=0),
+    dict(cluster=4, threads=512, chunk=256, n_vox=24, skip=0),
+    dict(cluster=2, threads=512, chunk=256, n_vox=24, prune=0, skip=0),
+    dict(cluster=2, threads=512, chunk=256, n_vox=20, radius_mode=1),
+    dict(n_vox=1),
+    dict(n_vox=256, chunk=32),
+]
+
+
+@pytest.mark.parametrize("opts", OPT_GRID, ids=[str(o) for o in OPT_GRID])
+def test_launch_shapes_and_switches(rf, opts):
+    """Every cluster size, CTA size, record chunk, resolution and switch gives the same indices."""
+    pts = cloudgen.room_cloud(12000, seed=11)
+    ref = oracle.fps(pts, 3000, 5, threads=0)
+    np.testing.assert_array_equal(gpu_fps(rf, pts, 3000, 5, **opts), ref)
+
+
+def test_shared_memory_overflow_path(rf):
+    """More records than one CTA holds in shared memory: the rest are read from global memory."""
+    pts = cloudgen.uniform_cloud(60000, seed=12)
+    ref = oracle.fps(pts, 2000, 0, threads=0)
+    # chunk 32 and 40^3 cells -> ~ (cells + N/32) records on a single CTA
+    np.testing.assert_array_equal(gpu_fps(rf, pts, 2000, 0, cluster=1, chunk=32, n_vox=40), ref)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 255, 257, 2047, 2049])
+def test_tiny_and_ragged_sizes(rf, n):
+    pts = cloudgen.uniform_cloud(n, seed=n)
+    for m in sorted({1, min(n, 2), n // 2 or 1, n}):
+        ref = oracle.fps(pts, m, n - 1)
+        np.testing.assert_array_equal(gpu_fps(rf, pts, m, n - 1), ref)
+
+
+def test_golden_examples(rf):
+    import json
+    import os
+    import pins
+    for case in json.load(open(os.path.join(pins.GOLDEN, "fps_hand_worked.json")))["cases"]:
+        pts = np.array(case["points"], dtype=np.float32)
+        if "points_bits" in case:
+            pts = np.array(case["points_bits"], dtype=np.uint32).view(np.float32)
+        for opts in ({}, {"n_vox": 2}, {"cluster": 2}):
+            got = gpu_fps(rf, pts, case["m"], case["start"], **opts)
+            assert got.tolist() == case["expected"], (case["name"], opts)
+        for v in (0, 1, 2):
+            got = rf.plain_fps(dev(pts), case["m"], case["start"], variant=v).cpu().numpy()
+            assert got.tolist() == case["expected"], (case["name"], "plain", v)
+
+
+def test_degenerate_clouds(rf):
+    same = np.tile(np.array([[1.5, -2.0, 7.0]], np.float32), (1000, 1))
+    np.testing.assert_array_equal(gpu_fps(rf, same, 10, 3), oracle.fps(same, 10, 3))
+    dup = cloudgen.uniform_cloud(50, seed=4)[np.random.default_rng(0).integers(0, 50, size=3000)]
+    np.testing.assert_array_equal(gpu_fps(rf, dup, 200, 0), oracle.fps(dup, 200, 0))
+    flat = cloudgen.uniform_cloud(5000, seed=5)
+    flat[:, 2] = 0.25
+    np.testing.assert_array_equal(gpu_fps(rf, flat, 1000, 0), oracle.fps(flat, 1000, 0))
+    line = np.zeros((4000, 3), np.float32)
+    line[:, 0] = np.linspace(-3, 5, 4000, dtype=np.float32)
+    np.testing.assert_array_equal(gpu_fps(rf, line, 4000, 0), oracle.fps(line, 4000, 0))
+    wide = cloudgen.uniform_cloud(4000, seed=6) * np.float32(1e15)
+    np.testing.assert_array_equal(gpu_fps(rf, wide, 800, 0), oracle.fps(wide, 800, 0))
+    tiny = cloudgen.uniform_cloud(4000, seed=7) * np.float32(1e-20)
+    np.testing.assert_array_equal(gpu_fps(rf, tiny, 800, 0), oracle.fps(tiny, 800, 0))
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_plain_variants(rf, variant):
+    for pts, m, start in ((cloudgen.uniform_cloud(4096, seed=0), 1024, 0),
+                          (cloudgen.room_cloud(50001, seed=9), 2000, 7)):
+        ref = oracle.fps(pts, m, start, threads=0)
+        got = rf.plain_fps(dev(pts), m, start, variant=variant).cpu().numpy()
+        np.testing.assert_array_equal(got, ref)
+
+
+def _ragged(sizes, seed):
+    clouds = []
+    for b, n in enumerate(sizes):
+        pts = cloudgen.room_cloud(n, seed=seed + b) if b % 2 == 0 else cloudgen.lidar_cloud(n, seed=seed + b)
+        clouds.append(pts)
+    return clouds
+
+
+@pytest.mark.parametrize("opts", [None, {"cluster": 2}, {"cluster": 4, "n_vox": 12}])
+def test_batched_matches_per_cloud_oracle(rf, opts):
+    sizes = [1, 7, 3000, 12345, 800, 20000, 64, 5000]
+    clouds = _ragged(sizes, 100)
+    ms = [max(1, n // 4) for n in sizes]
+    starts = [n // 3 for n in sizes]
+    cat = dev(np.concatenate(clouds))
+    out, ooff = rf.fps_batched(cat, sizes, ms, starts, opts=opts)
+    out = out.cpu().numpy()
+    for b, pts in enumerate(clouds):
+        ref = oracle.fps(pts, ms[b], starts[b], threads=0)
+        np.testing.assert_array_equal(out[ooff[b]:ooff[b + 1]], ref, err_msg=f"cloud {b}")
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_plain_batched(rf, variant):
+    sizes = [5, 3000, 12345, 800, 2048]
+    clouds = _ragged(sizes, 200)
+    ms = [max(1, n // 4) for n in sizes]
+    out, ooff = rf.plain_fps_batched(dev(np.concatenate(clouds)), sizes, ms, variant=variant)
+    out = out.cpu().numpy()
+    for b, pts in enumerate(clouds):
+        np.testing.assert_array_equal(out[ooff[b]:ooff[b + 1]], oracle.fps(pts, ms[b], 0, threads=0))
+
+
+def test_host_buffers(rf):
+    pts = cloudgen.room_cloud(30000, seed=21)
+    ref = oracle.fps(pts, 7000, 11, threads=0)
+    np.testing.assert_array_equal(rf.fps_host(pts, 7000, 11), ref)
+
+
+def test_index_reuse(rf):
+    pts = cloudgen.lidar_cloud(40000, seed=22)
+    ix = rf.Index(dev(pts))
+    for m, start in ((5000, 0), (100, 39999), (10000, 1234), (5000, 0)):
+        got = ix.sample(m, start).cpu().numpy()
+        np.testing.assert_array_equal(got, oracle.fps(pts, m, start, threads=0))
+    assert ix.nbytes > 0
+    ix.free()
+
+
+def test_index_matches_oracle_voxel_grid(rf):
+    """The device index agrees with the oracle's voxel grid (Sec. 3.2) bit for bit."""
+    pts = cloudgen.room_cloud(25000, seed=23)
+    for n_vox, chunk in ((16, 256), (33, 32)):
+        ix = rf.Index(dev(pts), opts={"n_vox": n_vox, "chunk": chunk})
+        e = ix.export()
+        grid, vid = oracle.voxelize(pts, n_vox)
+        assert e["n_vox"] == n_vox
+        assert np.array_equal(e["grid_min"], grid["min"]) and e["L"] == grid["L"]
+        orig = e["sorted_orig"]
+        assert sorted(orig.tolist()) == list(range(len(pts)))
+        # every record: one voxel, consecutive sorted positions, <= chunk points
+        pos_vid = np.empty(len(pts), np.uint32)
+        for r in range(len(e["first"])):
+            a, c = int(e["first"][r]), int(e["count"][r])
+            assert 1 <= c <= chunk
+            pos_vid[a:a + c] = e["voxel_id"][r]
+            members = orig[a:a + c]
+            assert np.all(vid[members] == e["voxel_id"][r])
+            # centre = p_min + (v + 1/2) L in FP32, radius covers every member exactly
+            v = int(e["voxel_id"][r])
+            vv = np.array([v % n_vox, (v // n_vox) % n_vox, v // (n_vox * n_vox)], np.float32)
+            cen = grid["min"] + (vv + np.float32(0.5)) * grid["L"]
+            assert np.array_equal(e["sphere"][r, :3], cen.astype(np.float32))
+            d = np.sqrt(((pts[members].astype(np.float64) - cen.astype(np.float64)) ** 2).sum(1)).max()
+            assert e["sphere"][r, 3] >= d and e["sphere"][r, 3] <= d * (1 + 2 ** -18) + 2 ** -49
+        assert np.array_equal(pos_vid, vid[orig])
+        # sorted by (voxel id, original index): stable grouping
+        key = vid[orig].astype(np.int64) * len(pts) + orig
+        assert np.all(np.diff(key) > 0)
+        ix.free()
+
+
+def test_nonfinite_is_reported(rf):
+    pts = cloudgen.uniform_cloud(1000, seed=3)
+    pts[500, 1] = np.nan
+    with pytest.raises(rf.RfpsError) as e:
+        rf.fps(dev(pts), 10, 0, check=True)
+    assert e.value.status == 2
+    pts[500, 1] = np.inf
+    with pytest.raises(rf.RfpsError):
+        rf.fps_host(pts, 10, 0)
+    # the workspace is usable again after the error
+    good = cloudgen.uniform_cloud(1000, seed=3)
+    np.testing.assert_array_equal(gpu_fps(rf, good, 100, 0), oracle.fps(good, 100, 0))
+
+
+def test_counters(rf):
+    """Pruning and skipping do real work on a room-like cloud (the Tab. ablation statistic)."""
+    pts = cloudgen.room_cloud(50000, seed=31)
+    ws = torch.empty(rf.workspace_size(50000, {"counters": 1}), dtype=torch.uint8, device="cuda")
+    out = rf.fps(dev(pts), 5000, 0, opts={"counters": 1}, workspace=ws)
+    c = rf.counters(ws)
+    np.testing.assert_array_equal(out.cpu().numpy(), oracle.fps(pts, 5000, 0, threads=0))
+    assert c["iterations"] == 4999
+    assert c["voxels_pruned"] > 0.8 * c["voxel_tests"]
+    assert c["points_skipped"] > 0 and c["points_updated"] > 50000
+    assert c["points_visited"] < 0.2 * 50000 * 4999
+
+
+def test_launch_counter_moves(rf):
+    before = rf.launch_count()
+    gpu_fps(rf, cloudgen.uniform_cloud(500, seed=1), 50)
+    assert rf.launch_count() > before
