@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -17,7 +18,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-BUILD = os.path.join(HERE, "_build")
+BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "librfps.so")
 SOURCES = ["rfps_api.cu", "rfps_build.cu", "rfps_sample.cu", "rfps_plain.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -65,11 +66,16 @@ def build(verbose: bool = False, force: bool = False) -> str:
             sys.stderr.write(r.stderr)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+    stamp = LIB + ".arch"
+    if not os.path.exists(stamp) or open(stamp).read().strip() != platform.machine():
+        force = True
     if force or _stale(LIB, objs):
         cmd = [cc, *ARCH, "-shared", "-o", LIB, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+        with open(stamp, "w") as fh:
+            fh.write(platform.machine())
     return LIB
 
 

@@ -19,9 +19,8 @@ def declared_functions():
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2606_06255_gb300 import build
-    if not os.path.exists(build.LIB):
-        build.build()
+    import __graft_entry__
+    __graft_entry__._builder().build()
     from paper_2606_06255_gb300 import _lib
     return _lib.lib()
 
