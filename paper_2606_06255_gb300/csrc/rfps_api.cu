@@ -66,11 +66,11 @@ rfps_opts resolve_opts(const rfps_opts* in, int64_t max_n)
     rfps_opts o;
     rfps_opts_default(&o);
     if (in) o = *in;
-    if (o.threads != 256 && o.threads != 512 && o.threads != 1024) o.threads = 512;
+    if (o.threads != 256 && o.threads != 512) o.threads = 512;
     if (o.cluster <= 0) {
         o.cluster = max_n <= 150000 ? 1 : (max_n <= 400000 ? 2 : (max_n <= 1000000 ? 4 : 8));
     }
-    if (o.chunk <= 0) o.chunk = 256;
+    if (o.chunk <= 0) o.chunk = 128;
     return o;
 }
 
@@ -106,6 +106,7 @@ WsLayout make_layout(int64_t total_n, int64_t n_clouds, int64_t max_n, const rfp
     L.rec_rng = take(N * 8);
     L.rec_key = take(N * 8);
     L.rec_best = take(N * 16);
+    L.rec_thr = take(N * 4);
     L.host_points = host_buffers ? take(N * 12) : 0;
     L.host_out = host_buffers ? take(static_cast<size_t>(host_m) * 8) : 0;
     L.total = off;
@@ -194,7 +195,7 @@ static rfps_status check_opts(const rfps_opts* o)
     if (o->cluster != 0 && o->cluster != 1 && o->cluster != 2 && o->cluster != 4 && o->cluster != 8 &&
         o->cluster != 16)
         return RFPS_EINVAL;
-    if (o->threads != 0 && o->threads != 256 && o->threads != 512 && o->threads != 1024) return RFPS_EINVAL;
+    if (o->threads != 0 && o->threads != 256 && o->threads != 512) return RFPS_EINVAL;
     if (o->chunk != 0 && (!is_pow2(o->chunk) || o->chunk < 32 || o->chunk > 4096)) return RFPS_EINVAL;
     if (o->radius_mode != 0 && o->radius_mode != 1) return RFPS_EINVAL;
     return RFPS_OK;

@@ -44,39 +44,42 @@ __device__ __forceinline__ unsigned long long make_key(float d2, uint32_t index)
 __device__ __forceinline__ float key_d2(unsigned long long key) { return __uint_as_float(static_cast<uint32_t>(key >> 32)); }
 __device__ __forceinline__ uint32_t key_index(unsigned long long key) { return ~static_cast<uint32_t>(key); }
 
-// Spherical-voxel radius pruning (Sec. 3.4.2: Eq. spherical_voxel_bound,
-// radius_pruning_condition), decided in FP32 with margins so that it is
-// safe for the FP32 squared distances it protects.  Returns true only if no
-// point of the record can get a strictly smaller stored distance from s.
+// Spherical-voxel radius pruning (Sec. 3.4.2: Eq. spherical_voxel_bound and
+// radius_pruning_condition) in FP32, decided without a square root per test.
 //
-// sph = (c_x, c_y, c_z, r): record centre and a radius with r >= |p - c| for
-// every member p (exact reals; guaranteed by the build, see record_radius).
-// key = the record's Dist_v key (max over its points).  u = 2^-24.
+// The paper prunes record k when LB = max(0, |s - c| - r) >= Dist_v, i.e.
+// when |s - c| >= r + sqrt(Dist_v).  Each record keeps a threshold T, computed
+// once whenever its Dist_v key changes, and a test is one canonical FP32 squared
+// distance and one compare: prune iff fl d2(s, c) >= T.
 //
-//   dc  = sqrt(fl d2(s, c))              <= (1+u)^3.5 |s - c| + 2^-74
-//   a   = fl(dc * (1 - 2^-20))           <= (1 - 11u) |s - c| + 2^-73
-//   lb  = fl(a - r)                      <= |s - c| - r_true  whenever
-//                                           lb^2 >= 2^-100 (then |s-c| >= 2^-51
-//                                           and the 10u|s-c| slack covers the
-//                                           subtraction's rounding and 2^-73)
-//   so |s - p| >= |s - c| - |p - c| >= lb for every member p, and
-//   fl d2(p, s) >= (1 - 5u) |s - p|^2 - 3 * 2^-150 >= (1 - 5u) lb^2 - 2^-148.
-//   test: t = fl(fl(lb*lb) * (1 - 2^-20)) <= (1 - 13u) lb^2.
-//   For lb^2 >= 2^-100 the 8u lb^2 gap exceeds 2^-148, hence
-//   fl d2(p, s) >= t >= Dist_v >= stored d2(p): the strict update cannot fire.
-// A record whose Dist_v is 0 cannot change either.  Non-finite lb^2 (huge
-// coordinates) never prunes.
-__device__ __forceinline__ bool prune_record(float4 sph, unsigned long long key, float sx, float sy, float sz)
+// Safety (u = 2^-24; r >= |p - c| for every member p, exact reals, from the
+// build; every rounding of T is upward, so T >= (r + rho)^2 (1 + 2^-20)):
+//   rho = sqrt(dv) (1 + 2^-20) (rounded up), so (1 - 5u) rho^2 >= dv (1 + 26u).
+//   fl d2(s, c) <= (1 + u)^5 |s - c|^2 + 3 * 2^-150; with T >= 2^-100 the
+//   test gives |s - c|^2 >= (r + rho)^2, so |s - p| >= |s - c| - |p - c|
+//   >= rho for every member p, and fl d2(p, s) >= (1 - 5u) rho^2 - 3 * 2^-150
+//   >= dv >= stored d2(p) when dv >= 2^-100: the strict update cannot fire.
+//   (An overflowed fl d2(s, c) = +inf only happens for |s - c|^2 above
+//   FLT_MAX / (1 + u)^5 >= T, so pruning on it is also safe.)
+// dv = 0: nothing can decrease, T = 0 always prunes.  dv tiny (< 2^-100) or
+// +inf, or T not finite: T = NaN, which never prunes.
+__device__ __forceinline__ float prune_threshold(float r, unsigned long long key)
 {
+    const float nan = __int_as_float(0x7fc00000);
     const float dv = key_d2(key);
-    if (dv == 0.0f) return true;
-    const float dc = __fsqrt_rn(sq_dist(sx, sy, sz, sph.x, sph.y, sph.z));
-    const float a = __fmul_rn(dc, 0x1.ffffep-1f);          // 1 - 2^-20
-    const float lb = __fsub_rn(a, sph.w);
-    if (!(lb > 0.0f)) return false;
-    const float lb2 = __fmul_rn(lb, lb);
-    if (!(lb2 >= 0x1p-100f) || !(lb2 <= 3.4028234e38f)) return false;
-    return __fmul_rn(lb2, 0x1.ffffep-1f) >= dv;
+    if (dv == 0.0f) return 0.0f;
+    if (!(dv >= 0x1p-100f) || !(dv <= 3.4028234e38f)) return nan;
+    const float rho = __fmul_ru(__fsqrt_ru(dv), 0x1.00001p0f);   // 1 + 2^-20
+    const float s = __fadd_ru(r, rho);
+    float t = __fmul_ru(__fmul_ru(s, s), 0x1.00001p0f);
+    t = fmaxf(t, 0x1p-100f);
+    return t <= 3.4028234e38f ? t : nan;
+}
+
+// The per-iteration test: record (centre, threshold) = ct.
+__device__ __forceinline__ bool prune_by_threshold(float4 ct, float sx, float sy, float sz)
+{
+    return sq_dist(sx, sy, sz, ct.x, ct.y, ct.z) >= ct.w;
 }
 
 // Coordinate-wise point skip (Sec. 3.4.3, Eq. point_skip_condition) in the

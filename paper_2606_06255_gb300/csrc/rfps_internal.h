@@ -55,7 +55,7 @@ struct WsLayout {
     size_t keys0, vals0, keys1, vals1;
     size_t hist, scan_agg, aux;
     size_t pts4, porig;
-    size_t rec_sph, rec_rng, rec_key, rec_best;
+    size_t rec_sph, rec_rng, rec_key, rec_best, rec_thr;
     size_t host_points, host_out;   // only for rfps_fps_host
     size_t total;
     int64_t total_n, n_clouds, max_records, radix_passes, radix_tiles;

@@ -12,16 +12,19 @@
 // points in the sorted float4 (x, y, z, d2) layout in global memory / L2.
 //
 // Iteration j (update with s_{j-1}, then select s_j):
-//   every warp takes a strided set of its CTA's records (adjacent records go
-//   to different warps); each lane tests one record with the FP-safe radius
-//   pruning bound (prune_record); the warp then walks the unpruned records of
-//   its lanes one by one: lanes stride over the record's points with the
-//   point skip, the exact update and the new record key (the Dist_v sync,
-//   Eq. point_skip_distv_sync);
-//   the max key over all records -- pruned records keep their key -- is
-//   reduced warp -> CTA (shared memory, one __syncthreads) -> cluster (each
-//   CTA pushes its best (key, x, y, z) into every CTA's shared memory, one
-//   barrier.cluster); every thread then knows s_j and its coordinates.
+//   every lane owns a fixed strided set of its CTA's records (adjacent
+//   records go to different warps) and tests them with the FP-safe radius
+//   pruning threshold (prune_threshold / prune_by_threshold: one squared
+//   distance and one compare per record, no square root); the warp then
+//   walks the unpruned records of its lanes one by one: lanes load the
+//   record's points with several loads in flight, apply the point skip, the
+//   exact update and form the new record key (the Dist_v sync, Eq.
+//   point_skip_distv_sync), and the record's threshold is recomputed;
+//   each lane caches the max key over the records it owns (keys only
+//   decrease, so it rescans only when the record holding its max changed);
+//   the max is reduced warp -> CTA (shared memory, one __syncthreads) ->
+//   cluster (each CTA pushes its best (key, x, y, z) into every CTA's shared
+//   memory, one barrier.cluster); every thread then knows s_j.
 // Iteration 1 is the initial update of Sec. 3.3: every record is visited and
 // the stored distances are treated as +inf, so a reused index needs no reset.
 // There is no per-iteration kernel launch and no global-memory round trip for
@@ -43,39 +46,174 @@ struct SampleArgs {
     const float* pts;          // caller's AoS points
     float4* pts4;              // sorted (x, y, z, d2)
     const uint32_t* porig;     // sorted position -> point row
-    const float4* rec_sph;
-    const uint2* rec_rng;
-    unsigned long long* rec_key;
-    float4* rec_best;
+    const float4* rec_sph;     // centre, covering radius (read-only after the build)
+    const uint2* rec_rng;      // first sorted position, count
+    unsigned long long* rec_key;   // Dist_v key
+    float4* rec_best;          // best point xyz, radius in .w (records kept in global memory)
+    float* rec_thr;            // prune threshold (records kept in global memory)
     int64_t* out;
-    uint32_t cap;              // records per CTA held in shared memory
+    size_t smem_bytes;         // dynamic shared memory per CTA
     int prune, skip;
+    int resident;              // 1: keep a CTA's points in shared memory when they fit
 };
 
 constexpr int kMaxCluster = 16;
+
+// Shared-memory record state of one CTA: ct = (centre, prune threshold),
+// best = (best point, covering radius), key = Dist_v key, rng = point range.
+struct RecView {
+    float4* ct;
+    float4* best;
+    unsigned long long* key;
+    uint2* rng;
+    uint32_t nsm, gbase, C;
+    const SampleArgs* a;
+    __device__ __forceinline__ bool smem(uint32_t l) const { return l < nsm; }
+    __device__ __forceinline__ uint32_t g(uint32_t l) const { return gbase + l * C; }
+    __device__ __forceinline__ float4 get_ct(uint32_t l) const
+    {
+        if (smem(l)) return ct[l];
+        const float4 s = a->rec_sph[g(l)];
+        return make_float4(s.x, s.y, s.z, a->rec_thr[g(l)]);
+    }
+    __device__ __forceinline__ unsigned long long get_key(uint32_t l) const
+    {
+        return smem(l) ? key[l] : a->rec_key[g(l)];
+    }
+    __device__ __forceinline__ float4 get_best(uint32_t l) const
+    {
+        return smem(l) ? best[l] : a->rec_best[g(l)];
+    }
+    __device__ __forceinline__ uint2 get_rng(uint32_t l) const { return smem(l) ? rng[l] : a->rec_rng[g(l)]; }
+    __device__ __forceinline__ float get_radius(uint32_t l) const
+    {
+        return smem(l) ? best[l].w : a->rec_sph[g(l)].w;
+    }
+    __device__ __forceinline__ void put(uint32_t l, unsigned long long k, float x, float y, float z, float r,
+                                        float thr) const
+    {
+        if (smem(l)) {
+            key[l] = k;
+            best[l] = make_float4(x, y, z, r);
+            ct[l].w = thr;
+        } else {
+            a->rec_key[g(l)] = k;
+            a->rec_best[g(l)] = make_float4(x, y, z, r);
+            a->rec_thr[g(l)] = thr;
+        }
+    }
+};
+
+struct Cnt {
+    uint64_t tests = 0, pruned = 0, visit = 0, skip = 0, upd = 0, iter = 0;
+};
+
+// One warp updates the points [off, off + cnt) of a record against s (point
+// skip, strict update, d2 write-back) and returns the lane's max key; the
+// lane's best point goes to (bx, by, bz).  `pts` / `orig` are either the CTA's
+// shared-memory copy or the workspace arrays.  PPL loads are in flight per lane.
+template <int PPL, bool COUNTERS>
+__device__ __forceinline__ unsigned long long visit_points(float4* pts, const uint32_t* orig, uint32_t off,
+                                                           uint32_t cnt, bool first, int skip, float sx, float sy,
+                                                           float sz, int lane, float& bx, float& by, float& bz,
+                                                           Cnt& k)
+{
+    unsigned long long lk = 0ull;
+    for (uint32_t q0 = 0; q0 < cnt; q0 += 32u * PPL) {
+        float4 p[PPL];
+        uint32_t gi[PPL];
+#pragma unroll
+        for (int u = 0; u < PPL; ++u) {
+            const uint32_t q = q0 + u * 32 + lane;
+            if (q < cnt) {
+                p[u] = pts[off + q];
+                gi[u] = orig[off + q];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PPL; ++u) {
+            const uint32_t q = q0 + u * 32 + lane;
+            if (q < cnt) {
+                float d2 = first ? __int_as_float(0x7f800000) : p[u].w;
+                const float dx = __fsub_rn(p[u].x, sx);
+                const float dy = __fsub_rn(p[u].y, sy);
+                const float dz = __fsub_rn(p[u].z, sz);
+                const float xx = __fmul_rn(dx, dx), yy = __fmul_rn(dy, dy), zz = __fmul_rn(dz, dz);
+                bool write = first;
+                if (skip && skip_point(xx, yy, zz, d2)) {
+                    if (COUNTERS) ++k.skip;
+                } else {
+                    const float nd = __fadd_rn(__fadd_rn(xx, yy), zz);
+                    if (nd < d2) {
+                        d2 = nd;
+                        write = true;
+                        if (COUNTERS) ++k.upd;
+                    }
+                }
+                if (write) pts[off + q].w = d2;
+                if (COUNTERS) ++k.visit;
+                const unsigned long long kk = make_key(d2, gi[u]);
+                if (kk > lk) {
+                    lk = kk;
+                    bx = p[u].x; by = p[u].y; bz = p[u].z;
+                }
+            }
+        }
+    }
+    return lk;
+}
+
+template <int NT>
+__device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t v, uint32_t* s_scr, uint32_t* total)
+{
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) s_scr[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t x = lane < NW ? s_scr[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
+        }
+        if (lane < NW) s_scr[lane] = x;
+    }
+    __syncthreads();
+    const uint32_t before = w > 0 ? s_scr[w - 1] : 0u;
+    *total = s_scr[NW - 1];
+    __syncthreads();
+    return before + inc - v;
+}
 
 template <int NT, bool CLUSTER, bool COUNTERS>
 __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
 {
     constexpr int NW = NT / 32;
+    constexpr int PPL = 4;                      // point loads in flight per lane
+    constexpr int NSLOT = CLUSTER ? kMaxCluster * NW : 1;
     extern __shared__ __align__(16) unsigned char smem[];
-    float4* s_sph = reinterpret_cast<float4*>(smem);
-    float4* s_best = s_sph + a.cap;
-    unsigned long long* s_key = reinterpret_cast<unsigned long long*>(s_best + a.cap);
-    uint2* s_rng = reinterpret_cast<uint2*>(s_key + a.cap);
     __shared__ unsigned long long s_wkey[2][NW];
     __shared__ uint32_t s_wrec[2][NW];
-    __shared__ unsigned long long s_ckey[2][kMaxCluster];
-    __shared__ float4 s_cxyz[2][kMaxCluster];
-    __shared__ uint32_t s_item;
+    __shared__ unsigned long long s_ckey[2][NSLOT];
+    __shared__ float4 s_cxyz[2][NSLOT];
+    __shared__ uint32_t s_scr[NW + 1];
+    __shared__ uint32_t s_item, s_wlc[2];
 
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const uint32_t rank = CLUSTER ? cluster_ctarank() : 0u;
     const uint32_t C = CLUSTER ? cluster_nctarank() : 1u;
     if (a.hdr->status != 0) return;   // same value in every CTA: uniform exit
     if (CLUSTER) cluster_sync();       // every CTA of the cluster is running before any DSMEM store
-
-    uint64_t c_tests = 0, c_pruned = 0, c_visit = 0, c_skip = 0, c_upd = 0, c_iter = 0;
+    const float nan = __int_as_float(0x7fc00000);
+    const uint32_t my = static_cast<uint32_t>(lane * NW + w);   // my slot inside each batch of NT records
+    Cnt cn;
 
     for (;;) {
         if (rank == 0 && t == 0) {
@@ -95,159 +233,321 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
         if (c.valid) {
             const uint32_t K = c.rec_end - c.rec_off;
             const uint32_t nloc = K > rank ? (K - rank + C - 1) / C : 0u;
-            const uint32_t nsm = nloc < a.cap ? nloc : a.cap;
             const uint32_t gbase = c.rec_off + rank;
-            for (uint32_t l = t; l < nsm; l += NT) {
-                const uint32_t k = gbase + l * C;
-                s_sph[l] = a.rec_sph[k];
-                s_rng[l] = a.rec_rng[k];
-                s_key[l] = a.rec_key[k];
-                s_best[l] = a.rec_best[k];
+            // Fast path: every record of this CTA in shared memory (52 bytes each),
+            // then as many points as fit (20 bytes each).
+            const bool fast = static_cast<size_t>(nloc) * 52 + 16 <= a.smem_bytes && nloc <= 32u * NT;
+            RecView v;
+            v.a = &a;
+            v.C = C;
+            v.gbase = gbase;
+            float4* s_pts = nullptr;
+            uint32_t* s_orig = nullptr;
+            uint32_t* s_wl = nullptr;
+            bool resident = false;
+            if (fast) {
+                v.nsm = nloc;
+                v.ct = reinterpret_cast<float4*>(smem);
+                v.best = v.ct + nloc;
+                v.key = reinterpret_cast<unsigned long long*>(v.best + nloc);
+                v.rng = reinterpret_cast<uint2*>(v.key + nloc);
+                s_wl = reinterpret_cast<uint32_t*>(v.rng + nloc);
+                const size_t poff = (static_cast<size_t>(nloc) * 52 + 15) & ~static_cast<size_t>(15);
+                s_pts = reinterpret_cast<float4*>(smem + poff);
+                const uint32_t P = static_cast<uint32_t>((a.smem_bytes - poff) / 20);
+                s_orig = reinterpret_cast<uint32_t*>(s_pts + P);
+                uint32_t mine = 0;
+                for (uint32_t l = t; l < nloc; l += NT) {
+                    const uint32_t k = v.g(l);
+                    const float4 sph = a.rec_sph[k];
+                    const uint2 rg = a.rec_rng[k];
+                    v.ct[l] = make_float4(sph.x, sph.y, sph.z, nan);
+                    v.best[l] = make_float4(0.f, 0.f, 0.f, sph.w);
+                    v.key[l] = 0ull;
+                    v.rng[l] = rg;
+                    mine += rg.y;
+                }
+                uint32_t total;
+                block_exclusive_sum<NT>(mine, s_scr, &total);
+                resident = a.resident && total <= P;
+                if (resident) {
+                    // shared-memory offsets of my records: contiguous chunks per thread, then a block scan
+                    const uint32_t per = (nloc + NT - 1) / NT;
+                    const uint32_t l0 = min(nloc, t * per), l1 = min(nloc, l0 + per);
+                    uint32_t sum = 0;
+                    for (uint32_t l = l0; l < l1; ++l) sum += v.rng[l].y;
+                    uint32_t off = block_exclusive_sum<NT>(sum, s_scr, &total);
+                    for (uint32_t l = l0; l < l1; ++l) {
+                        const uint32_t cnt = v.rng[l].y;
+                        s_wl[l] = off;       // staging: the worklist is not in use yet
+                        off += cnt;
+                    }
+                    __syncthreads();
+                    for (uint32_t l = w; l < nloc; l += NW) {
+                        const uint2 rg = v.rng[l];
+                        const uint32_t so = s_wl[l];
+                        for (uint32_t q = lane; q < rg.y; q += 32) {
+                            s_pts[so + q] = a.pts4[rg.x + q];
+                            s_orig[so + q] = a.porig[rg.x + q];
+                        }
+                    }
+                    __syncthreads();
+                    for (uint32_t l = t; l < nloc; l += NT) v.rng[l].x = s_wl[l];
+                }
+            } else {
+                v.nsm = static_cast<uint32_t>(a.smem_bytes / 48);
+                if (v.nsm > nloc) v.nsm = nloc;
+                v.ct = reinterpret_cast<float4*>(smem);
+                v.best = v.ct + v.nsm;
+                v.key = reinterpret_cast<unsigned long long*>(v.best + v.nsm);
+                v.rng = reinterpret_cast<uint2*>(v.key + v.nsm);
+                for (uint32_t l = t; l < nloc; l += NT) {
+                    const uint32_t k = v.g(l);
+                    const float4 sph = a.rec_sph[k];
+                    if (l < v.nsm) {
+                        v.ct[l] = make_float4(sph.x, sph.y, sph.z, nan);
+                        v.best[l] = make_float4(0.f, 0.f, 0.f, sph.w);
+                        v.key[l] = 0ull;
+                        v.rng[l] = a.rec_rng[k];
+                    } else {
+                        a.rec_thr[k] = nan;
+                        a.rec_best[k] = make_float4(0.f, 0.f, 0.f, sph.w);
+                        a.rec_key[k] = 0ull;
+                    }
+                }
             }
             const int64_t g0 = c.pt_off + c.start;
             float sx = a.pts[3 * g0 + 0], sy = a.pts[3 * g0 + 1], sz = a.pts[3 * g0 + 2];
+            if (t == 0) {
+                s_wlc[0] = 0;   // every CTA's own worklist counters
+                s_wlc[1] = 0;
+            }
             if (rank == 0 && t == 0) a.out[c.out_off] = c.start;
+            // this lane's cached max over the records it owns (my, my + NT, ...)
+            unsigned long long lkey = 0ull;
+            uint32_t lrec = 0xffffffffu;
+            bool dirty = true;
             __syncthreads();
 
             for (int64_t j = 1; j < c.m; ++j) {
                 const bool first = (j == 1);
                 const int par = static_cast<int>(j & 1);
-                unsigned long long tk = 0ull;
-                uint32_t tr = 0xffffffffu;
-                for (uint32_t base = 0; base < nloc; base += NT) {
-                    const uint32_t l = base + static_cast<uint32_t>(lane * NW + w);
-                    const bool valid = l < nloc;
-                    bool visit = false;
-                    if (valid) {
-                        const bool in_smem = l < nsm;
-                        const float4 sph = in_smem ? s_sph[l] : a.rec_sph[gbase + l * C];
-                        const unsigned long long key = in_smem ? s_key[l] : a.rec_key[gbase + l * C];
-                        visit = first || !a.prune || !prune_record(sph, key, sx, sy, sz);
-                        if (!visit && key > tk) {
-                            tk = key;
-                            tr = l;
-                        }
-                        if (COUNTERS) {
-                            c_tests += first ? 0 : 1;
-                            c_pruned += visit ? 0 : 1;
+                unsigned long long pk;   // this lane's partial max (key, record) for the selection
+                uint32_t prec;
+                if (fast) {
+                    // ---- prune test of my records; unpruned ones go to the CTA worklist
+                    const int nb = static_cast<int>((nloc + NT - 1) / NT);
+                    uint32_t um = 0;
+                    for (int b = 0; b < nb; ++b) {
+                        const uint32_t l = static_cast<uint32_t>(b) * NT + my;
+                        if (l < nloc) {
+                            const bool keep = first || !a.prune || !prune_by_threshold(v.ct[l], sx, sy, sz);
+                            um |= keep ? (1u << b) : 0u;
+                            if (COUNTERS && !first) {
+                                ++cn.tests;
+                                cn.pruned += keep ? 0 : 1;
+                            }
                         }
                     }
-                    unsigned mask = __ballot_sync(0xffffffffu, visit);
-                    while (mask) {
-                        const int src = __ffs(mask) - 1;
-                        mask &= mask - 1;
-                        const uint32_t lr = __shfl_sync(0xffffffffu, l, src);
-                        const bool in_smem = lr < nsm;
-                        const uint2 rng = in_smem ? s_rng[lr] : a.rec_rng[gbase + lr * C];
-                        unsigned long long lk = 0ull;
-                        float bx = 0.f, by = 0.f, bz = 0.f;
-                        for (uint32_t q = lane; q < rng.y; q += 32) {
-                            const uint32_t pos = rng.x + q;
-                            const float4 p = a.pts4[pos];
-                            const uint32_t g = a.porig[pos];
-                            float d2 = first ? __int_as_float(0x7f800000) : p.w;
-                            const float dx = __fsub_rn(p.x, sx);
-                            const float dy = __fsub_rn(p.y, sy);
-                            const float dz = __fsub_rn(p.z, sz);
-                            const float xx = __fmul_rn(dx, dx), yy = __fmul_rn(dy, dy), zz = __fmul_rn(dz, dz);
-                            if (a.skip && skip_point(xx, yy, zz, d2)) {
-                                if (COUNTERS) ++c_skip;
-                                if (first) a.pts4[pos].w = d2;
-                            } else {
-                                const float nd = __fadd_rn(__fadd_rn(xx, yy), zz);
-                                if (nd < d2) {
-                                    d2 = nd;
-                                    if (COUNTERS) ++c_upd;
-                                    a.pts4[pos].w = d2;
-                                } else if (first) {
-                                    a.pts4[pos].w = d2;
+                    const uint32_t nkeep = __popc(um);
+                    uint32_t incl = nkeep;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += u;
+                    }
+                    const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+                    if (wtot) {
+                        uint32_t base = 0;
+                        if (lane == 31) base = atomicAdd(&s_wlc[par], wtot);
+                        base = __shfl_sync(0xffffffffu, base, 31);
+                        uint32_t pos = base + incl - nkeep;
+                        for (uint32_t mm = um; mm; mm &= mm - 1) s_wl[pos++] = static_cast<uint32_t>(__ffs(mm) - 1) * NT + my;
+                    }
+                    // ---- partial max over my records that are not revisited this iteration
+                    const bool lrec_visited = lrec != 0xffffffffu && ((um >> (lrec / NT)) & 1u);
+                    if (dirty || lrec_visited) {
+                        lkey = 0ull;
+                        lrec = 0xffffffffu;
+                        for (int b = 0; b < nb; ++b) {
+                            const uint32_t l = static_cast<uint32_t>(b) * NT + my;
+                            if (l < nloc && !((um >> b) & 1u)) {
+                                const unsigned long long kk = v.key[l];
+                                if (kk > lkey) {
+                                    lkey = kk;
+                                    lrec = l;
                                 }
                             }
-                            if (COUNTERS) ++c_visit;
-                            const unsigned long long k = make_key(d2, g);
-                            if (k > lk) {
-                                lk = k;
-                                bx = p.x; by = p.y; bz = p.z;
-                            }
                         }
+                    }
+                    dirty = um != 0;
+                    pk = lkey;
+                    prec = lrec;
+                    __syncthreads();
+                    if (t == 0) s_wlc[par ^ 1] = 0;
+                    // ---- one warp per unpruned record
+                    const uint32_t nwl = s_wlc[par];
+                    for (uint32_t i = w; i < nwl; i += NW) {
+                        const uint32_t l = s_wl[i];
+                        const uint2 rg = v.rng[l];
+                        float bx = 0.f, by = 0.f, bz = 0.f;
+                        const unsigned long long lk =
+                            resident ? visit_points<PPL, COUNTERS>(s_pts, s_orig, rg.x, rg.y, first, a.skip, sx, sy,
+                                                                   sz, lane, bx, by, bz, cn)
+                                     : visit_points<PPL, COUNTERS>(a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx,
+                                                                   sy, sz, lane, bx, by, bz, cn);
                         unsigned long long rk;
                         const int wl = warp_argmax_lane(lk, &rk);
                         const float wx = __shfl_sync(0xffffffffu, bx, wl);
                         const float wy = __shfl_sync(0xffffffffu, by, wl);
                         const float wz = __shfl_sync(0xffffffffu, bz, wl);
                         if (lane == 0) {
-                            if (in_smem) {
-                                s_key[lr] = rk;
-                                s_best[lr] = make_float4(wx, wy, wz, 0.f);
-                            } else {
-                                a.rec_key[gbase + lr * C] = rk;
-                                a.rec_best[gbase + lr * C] = make_float4(wx, wy, wz, 0.f);
+                            const float r = v.best[l].w;
+                            v.key[l] = rk;
+                            v.best[l] = make_float4(wx, wy, wz, r);
+                            v.ct[l].w = prune_threshold(r, rk);
+                            if (rk > pk) {
+                                pk = rk;
+                                prec = l;
                             }
                         }
-                        if (lane == src && rk > tk) {
-                            tk = rk;
-                            tr = lr;
+                    }
+                } else {
+                    // ---- records partly in global memory: each warp visits its lanes' unpruned records
+                    for (uint32_t g0r = 0; g0r < nloc; g0r += 32u * NT) {
+                        uint32_t um = 0;
+#pragma unroll 4
+                        for (int b = 0; b < 32; ++b) {
+                            const uint32_t l = g0r + static_cast<uint32_t>(b) * NT + my;
+                            if (l < nloc) {
+                                const bool keep = first || !a.prune || !prune_by_threshold(v.get_ct(l), sx, sy, sz);
+                                um |= keep ? (1u << b) : 0u;
+                                if (COUNTERS && !first) {
+                                    ++cn.tests;
+                                    cn.pruned += keep ? 0 : 1;
+                                }
+                            }
+                        }
+                        uint32_t wm = __reduce_or_sync(0xffffffffu, um);
+                        while (wm) {
+                            const int b = __ffs(wm) - 1;
+                            wm &= wm - 1;
+                            uint32_t mask = __ballot_sync(0xffffffffu, (um >> b) & 1u);
+                            while (mask) {
+                                const int src = __ffs(mask) - 1;
+                                mask &= mask - 1;
+                                const uint32_t lr =
+                                    g0r + static_cast<uint32_t>(b) * NT + static_cast<uint32_t>(src * NW + w);
+                                const uint2 rg = v.get_rng(lr);
+                                float bx = 0.f, by = 0.f, bz = 0.f;
+                                const unsigned long long lk = visit_points<PPL, COUNTERS>(
+                                    a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx, sy, sz, lane, bx, by, bz, cn);
+                                unsigned long long rk;
+                                const int wl = warp_argmax_lane(lk, &rk);
+                                const float wx = __shfl_sync(0xffffffffu, bx, wl);
+                                const float wy = __shfl_sync(0xffffffffu, by, wl);
+                                const float wz = __shfl_sync(0xffffffffu, bz, wl);
+                                if (lane == 0) {
+                                    const float r = v.get_radius(lr);
+                                    v.put(lr, rk, wx, wy, wz, r, prune_threshold(r, rk));
+                                }
+                                // keys only decrease: the owner's cached max needs a rescan only
+                                // if this record held it
+                                if (lane == src && lr == lrec) dirty = true;
+                            }
                         }
                     }
+                    __syncwarp();
+                    if (dirty) {
+                        lkey = 0ull;
+                        lrec = 0xffffffffu;
+                        for (uint32_t l = my; l < nloc; l += NT) {
+                            const unsigned long long kk = v.get_key(l);
+                            if (kk > lkey) {
+                                lkey = kk;
+                                lrec = l;
+                            }
+                        }
+                    }
+                    dirty = false;
+                    pk = lkey;
+                    prec = lrec;
                 }
-                // warp -> CTA
+                // ---- selection: warp -> CTA -> cluster
+                __syncwarp();
                 unsigned long long wk;
-                const int wl = warp_argmax_lane(tk, &wk);
-                const uint32_t wr = __shfl_sync(0xffffffffu, tr, wl);
-                if (lane == 0) {
-                    s_wkey[par][w] = wk;
-                    s_wrec[par][w] = wr;
-                }
-                __syncthreads();
-                unsigned long long ck = lane < NW ? s_wkey[par][lane] : 0ull;
-                uint32_t cr = lane < NW ? s_wrec[par][lane] : 0xffffffffu;
-                unsigned long long cbest;
-                const int cl = warp_argmax_lane(ck, &cbest);
-                cr = __shfl_sync(0xffffffffu, cr, cl);
+                const int wl = warp_argmax_lane(pk, &wk);
+                const uint32_t wr = __shfl_sync(0xffffffffu, prec, wl);
                 float4 cxyz = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (cbest != 0ull) cxyz = cr < nsm ? s_best[cr] : a.rec_best[gbase + cr * C];
-                unsigned long long gbest = cbest;
-                if (CLUSTER) {
-                    // CTA -> cluster: push (key, xyz) into slot `rank` of every CTA
-                    if (w == 0 && lane < static_cast<int>(C)) {
-                        st_cluster_u64(map_shared(&s_ckey[par][rank], lane), cbest);
-                        st_cluster_f32x4(map_shared(&s_cxyz[par][rank], lane), cxyz);
+                unsigned long long gbest;
+                if (!CLUSTER) {
+                    if (lane == 0) {
+                        s_wkey[par][w] = wk;
+                        s_wrec[par][w] = wr;
+                    }
+                    __syncthreads();
+                    const unsigned long long ck = lane < NW ? s_wkey[par][lane] : 0ull;
+                    uint32_t cr = lane < NW ? s_wrec[par][lane] : 0xffffffffu;
+                    const int cl = warp_argmax_lane(ck, &gbest);
+                    cr = __shfl_sync(0xffffffffu, cr, cl);
+                    if (gbest != 0ull) cxyz = fast ? v.best[cr] : v.get_best(cr);
+                } else {
+                    // every warp pushes its best (key, xyz) into slot [rank][warp] of every CTA
+                    float4 wxyz = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (wk != 0ull && lane < static_cast<int>(C)) wxyz = fast ? v.best[wr] : v.get_best(wr);
+                    if (lane < static_cast<int>(C)) {
+                        st_cluster_u64(map_shared(&s_ckey[par][rank * NW + w], lane), wk);
+                        st_cluster_f32x4(map_shared(&s_cxyz[par][rank * NW + w], lane), wxyz);
                     }
                     cluster_sync();
-                    const unsigned long long kk = lane < static_cast<int>(C) ? s_ckey[par][lane] : 0ull;
+                    unsigned long long kk = 0ull;
+                    uint32_t ki = 0;
+                    for (uint32_t q = lane; q < C * NW; q += 32) {
+                        const unsigned long long x = s_ckey[par][q];
+                        if (x > kk) {
+                            kk = x;
+                            ki = q;
+                        }
+                    }
                     const int gl = warp_argmax_lane(kk, &gbest);
-                    cxyz = s_cxyz[par][gl];
+                    ki = __shfl_sync(0xffffffffu, ki, gl);
+                    cxyz = s_cxyz[par][ki];
                 }
                 sx = cxyz.x;
                 sy = cxyz.y;
                 sz = cxyz.z;
                 if (rank == 0 && t == 0)
                     a.out[c.out_off + j] = static_cast<int64_t>(key_index(gbest)) - c.pt_off;
-                if (COUNTERS) ++c_iter;
+                if (COUNTERS) ++cn.iter;
             }
         }
         if (CLUSTER) cluster_sync(); else __syncthreads();
     }
     if (COUNTERS) {
-        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[0]), c_tests);
-        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[1]), c_pruned);
-        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[2]), c_visit);
-        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[3]), c_skip);
-        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[4]), c_upd);
-        if (t == 0 && rank == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[5]), c_iter);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[0]), cn.tests);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[1]), cn.pruned);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[2]), cn.visit);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[3]), cn.skip);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[4]), cn.upd);
+        if (t == 0 && rank == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[5]), cn.iter);
     }
 }
 
 template <int NT, bool CLUSTER, bool COUNTERS>
-cudaError_t launch_one(const SampleArgs& args, int C, int64_t n_clouds, cudaStream_t st)
+cudaError_t launch_one(SampleArgs args, int C, int64_t n_clouds, cudaStream_t st)
 {
     auto kern = k_sample<NT, CLUSTER, COUNTERS>;
-    const size_t dyn = static_cast<size_t>(args.cap) * 48;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
+    int dev = 0, sms = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    const size_t dyn = static_cast<size_t>(optin) - fa.sharedSizeBytes - 1024;
+    args.smem_bytes = dyn;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.blockDim = dim3(NT);
@@ -289,11 +589,8 @@ cudaError_t launch_one(const SampleArgs& args, int C, int64_t n_clouds, cudaStre
 template <bool CLUSTER, bool COUNTERS>
 cudaError_t launch_nt(const SampleArgs& args, int NT, int C, int64_t n_clouds, cudaStream_t st)
 {
-    switch (NT) {
-    case 256: return launch_one<256, CLUSTER, COUNTERS>(args, C, n_clouds, st);
-    case 512: return launch_one<512, CLUSTER, COUNTERS>(args, C, n_clouds, st);
-    default: return launch_one<1024, CLUSTER, COUNTERS>(args, C, n_clouds, st);
-    }
+    return NT == 256 ? launch_one<256, CLUSTER, COUNTERS>(args, C, n_clouds, st)
+                     : launch_one<512, CLUSTER, COUNTERS>(args, C, n_clouds, st);
 }
 
 }  // namespace
@@ -314,12 +611,12 @@ cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int6
     a.rec_rng = reinterpret_cast<const uint2*>(ws + L.rec_rng);
     a.rec_key = reinterpret_cast<unsigned long long*>(ws + L.rec_key);
     a.rec_best = reinterpret_cast<float4*>(ws + L.rec_best);
+    a.rec_thr = reinterpret_cast<float*>(ws + L.rec_thr);
     a.out = out;
     a.prune = o.prune;
     a.skip = o.skip;
-    // shared memory: as many records as fit beside the static slots
-    const size_t budget = 200 * 1024;
-    a.cap = static_cast<uint32_t>(budget / 48);
+    a.smem_bytes = 0;   // set per instantiation from the device's opt-in limit
+    a.resident = 1;
     const int C = o.cluster;
     const bool cl = C > 1;
     if (o.counters) {

@@ -63,6 +63,8 @@ def test_workspace_sizes_are_host_only(lib):
     assert lib.rfps_fps_workspace_size(1000, ctypes.byref(bad)) == 0
     bad = Opts(cluster=3)
     assert lib.rfps_fps_workspace_size(1000, ctypes.byref(bad)) == 0
+    bad = Opts(threads=1024)
+    assert lib.rfps_fps_workspace_size(1000, ctypes.byref(bad)) == 0
 
 
 def test_argument_errors_need_no_device(lib):

@@ -48,10 +48,10 @@ def test_default_path_matches_oracle(rf, name, make, m, start):
 
 OPT_GRID = [
     dict(cluster=1, threads=256, chunk=32, n_vox=4),
-    dict(cluster=1, threads=1024, chunk=4096, n_vox=64),
+    dict(cluster=1, threads=512, chunk=4096, n_vox=64),
     dict(cluster=2, threads=512, chunk=64, n_vox=16),
     dict(cluster=4, threads=256, chunk=256, n_vox=32),
-    dict(cluster=8, threads=1024, chunk=128, n_vox=8),
+    dict(cluster=8, threads=256, chunk=128, n_vox=8),
     dict(cluster=16, threads=512, chunk=512, n_vox=48),
     dict(cluster=4, threads=512, chunk=256, n_vox=24, prune=0),
     dict(cluster=4, threads=512, chunk=256, n_vox=24, skip=0),
