@@ -185,6 +185,21 @@ rfps_status rfps_plain_fps_batched(const float *points, int64_t total_n,
                                    void *stream);
 
 /* ------------------------------------------------------------------------
+ * Measurement of the sampling loop's synchronisation floor: one CTA cluster
+ * of `cluster` CTAs x `threads` threads runs `iterations` rounds of exactly
+ * the selection step of the RadiusFPS kernel (warp argmax, CTA reduction, the
+ * DSMEM exchange and one barrier per round) with no voxel or point work.
+ * The caller times the launch (e.g. CUDA events on `stream`); time divided by
+ * iterations is the per-iteration floor of the sampling loop (Sec. 4.2's
+ * "only synchronization point" of each iteration).  `workspace`: device, at
+ * least 136 bytes, 256-byte aligned: one value per CTA (16 x 8 bytes), then a
+ * status word (RFPS_ETIMEOUT if a bounded wait gave up; the caller zeroes it).
+ * cluster in {1, 2, 4, 8, 16}, threads in {256, 512}.
+ * ---------------------------------------------------------------------- */
+rfps_status rfps_sync_floor(int32_t cluster, int32_t threads, int64_t iterations,
+                            void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
  * Device status and counters of a workspace.  Both synchronise `stream`.
  * rfps_status_read returns the first error the device recorded for the last
  * call that used `workspace` (RFPS_OK if none).

@@ -22,5 +22,6 @@ from ._lib import (  # noqa: F401
     plain_fps_batched,
     plain_workspace_size,
     status,
+    sync_floor,
     workspace_size,
 )

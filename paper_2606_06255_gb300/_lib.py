@@ -76,6 +76,7 @@ def _load():
         "rfps_plain_fps": (st, [vp, i64, i64, i64, vp, i32, vp, sz, vp]),
         "rfps_plain_fps_batched": (st, [vp, i64, vp, i64, vp, vp, i64, vp, i32, vp, sz, vp]),
         "rfps_status_read": (st, [vp, vp]),
+        "rfps_sync_floor": (st, [i32, i32, i64, vp, sz, vp]),
         "rfps_counters_read": (st, [vp, ctypes.POINTER(Counters), vp]),
         "rfps_index_build": (st, [vp, i64, optp, ctypes.POINTER(vp), vp]),
         "rfps_index_sample": (st, [vp, i64, i64, vp, vp]),
@@ -247,6 +248,24 @@ def counters(workspace: torch.Tensor, stream=None) -> dict:
     c = Counters()
     _check(_lib.rfps_counters_read(workspace.data_ptr(), ctypes.byref(c), _stream(stream)), "rfps_counters_read")
     return c.as_dict()
+
+
+def sync_floor(cluster: int, threads: int, iterations: int, stream=None) -> float:
+    """Milliseconds of `iterations` rounds of the sampling loop's selection step alone (CUDA events)."""
+    ws = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream() if stream is None else stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    _check(_lib.rfps_sync_floor(cluster, threads, iterations, ws.data_ptr(), ws.numel(), _stream(st)),
+           "rfps_sync_floor")
+    e0.record(st)
+    _check(_lib.rfps_sync_floor(cluster, threads, iterations, ws.data_ptr(), ws.numel(), _stream(st)),
+           "rfps_sync_floor")
+    e1.record(st)
+    e1.synchronize()
+    if int(ws[128:132].view(torch.int32).item()) != 0:
+        raise RfpsError(ETIMEOUT, "rfps_sync_floor (device)")
+    return e0.elapsed_time(e1)
 
 
 def launch_count() -> int:

@@ -340,6 +340,19 @@ rfps_status rfps_plain_fps_batched(const float* points, int64_t total_n, const i
                         workspace, workspace_bytes, stream);
 }
 
+rfps_status rfps_sync_floor(int32_t cluster, int32_t threads, int64_t iterations, void* workspace,
+                            size_t workspace_bytes, void* stream)
+{
+    if (!workspace || iterations < 1 || (threads != 256 && threads != 512) ||
+        (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8 && cluster != 16) ||
+        workspace_bytes < 17 * sizeof(unsigned long long) || !aligned256(workspace))
+        return RFPS_EINVAL;
+    rfps_status s = device_check();
+    if (s != RFPS_OK) return s;
+    return from_cuda(launch_sync_floor(cluster, threads, iterations, static_cast<unsigned long long*>(workspace),
+                                       static_cast<cudaStream_t>(stream)));
+}
+
 rfps_status rfps_status_read(const void* workspace, void* stream)
 {
     if (!workspace) return RFPS_EINVAL;

@@ -73,6 +73,8 @@ cudaError_t launch_build(char* ws, const WsLayout& L, const float* points, const
 // Persistent sampling launch over the clouds of ws.
 cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int64_t* out,
                           const rfps_opts& o, int64_t n_clouds, int64_t max_n, cudaStream_t st);
+// Synchronisation floor of the sampling loop (same tail, no record work).
+cudaError_t launch_sync_floor(int C, int NT, int64_t iters, unsigned long long* sink, cudaStream_t st);
 // Plain FPS launches.
 cudaError_t launch_plain(char* ws, const WsLayout& L, const float* points, int64_t* out, int variant,
                          int64_t n_clouds, int64_t max_n, cudaStream_t st);

@@ -58,6 +58,7 @@ struct SampleArgs {
 };
 
 constexpr int kMaxCluster = 16;
+constexpr uint32_t kSpinLimit = 1u << 22;   // try_wait rounds before a wait gives up
 
 // Shared-memory record state of one CTA: ct = (centre, prune threshold),
 // best = (best point, covering radius), key = Dist_v key, rng = point range.
@@ -204,13 +205,24 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
     __shared__ unsigned long long s_ckey[2][NSLOT];
     __shared__ float4 s_cxyz[2][NSLOT];
     __shared__ uint32_t s_scr[NW + 1];
-    __shared__ uint32_t s_item, s_wlc[2];
+    __shared__ uint32_t s_item, s_wlc[2], s_abort;
+    __shared__ unsigned long long s_mbar[2];
 
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const uint32_t rank = CLUSTER ? cluster_ctarank() : 0u;
     const uint32_t C = CLUSTER ? cluster_nctarank() : 1u;
     if (a.hdr->status != 0) return;   // same value in every CTA: uniform exit
-    if (CLUSTER) cluster_sync();       // every CTA of the cluster is running before any DSMEM store
+    if (t == 0) {
+        s_abort = 0;
+        if (CLUSTER) {
+            mbar_init(&s_mbar[0], 1);
+            mbar_init(&s_mbar[1], 1);
+            fence_mbar_init_cluster();
+        }
+    }
+    if (CLUSTER) cluster_sync();       // barriers initialised, every CTA running before any DSMEM store
+    else __syncthreads();
+    uint32_t it = 0;                   // exchange rounds so far (same count in every CTA of the cluster)
     const float nan = __int_as_float(0x7fc00000);
     const uint32_t my = static_cast<uint32_t>(lane * NW + w);   // my slot inside each batch of NT records
     Cnt cn;
@@ -384,6 +396,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     pk = lkey;
                     prec = lrec;
                     __syncthreads();
+                    if (CLUSTER && s_abort) break;   // uniform: read after the barrier
                     if (t == 0) s_wlc[par ^ 1] = 0;
                     // ---- one warp per unpruned record
                     const uint32_t nwl = s_wlc[par];
@@ -413,6 +426,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         }
                     }
                 } else {
+                    if (CLUSTER && __syncthreads_or(s_abort != 0)) break;
                     // ---- records partly in global memory: each warp visits its lanes' unpruned records
                     for (uint32_t g0r = 0; g0r < nloc; g0r += 32u * NT) {
                         uint32_t um = 0;
@@ -492,18 +506,26 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     cr = __shfl_sync(0xffffffffu, cr, cl);
                     if (gbest != 0ull) cxyz = fast ? v.best[cr] : v.get_best(cr);
                 } else {
-                    // every warp pushes its best (key, xyz) into slot [rank][warp] of every CTA
+                    // every warp pushes its best (key, xyz) into slot [rank][warp] of every CTA with
+                    // st.async; each CTA's barrier for this round expects C * NW * 24 bytes
+                    const uint32_t buf = it & 1u, ph = (it >> 1) & 1u;
+                    ++it;
+                    if (t == 0) mbar_arrive_expect_tx(&s_mbar[buf], 24u * C * NW);
                     float4 wxyz = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (wk != 0ull && lane < static_cast<int>(C)) wxyz = fast ? v.best[wr] : v.get_best(wr);
                     if (lane < static_cast<int>(C)) {
-                        st_cluster_u64(map_shared(&s_ckey[par][rank * NW + w], lane), wk);
-                        st_cluster_f32x4(map_shared(&s_cxyz[par][rank * NW + w], lane), wxyz);
+                        const uint32_t rb = map_shared(&s_mbar[buf], lane);
+                        st_async_u64(map_shared(&s_ckey[buf][rank * NW + w], lane), wk, rb);
+                        st_async_f32x4(map_shared(&s_cxyz[buf][rank * NW + w], lane), wxyz, rb);
                     }
-                    cluster_sync();
+                    if (!mbar_wait_bounded(&s_mbar[buf], ph, kSpinLimit)) {
+                        atomicCAS(&a.hdr->status, 0u, kStatusTimeout);
+                        s_abort = 1;
+                    }
                     unsigned long long kk = 0ull;
                     uint32_t ki = 0;
                     for (uint32_t q = lane; q < C * NW; q += 32) {
-                        const unsigned long long x = s_ckey[par][q];
+                        const unsigned long long x = s_ckey[buf][q];
                         if (x > kk) {
                             kk = x;
                             ki = q;
@@ -511,7 +533,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     }
                     const int gl = warp_argmax_lane(kk, &gbest);
                     ki = __shfl_sync(0xffffffffu, ki, gl);
-                    cxyz = s_cxyz[par][ki];
+                    cxyz = s_cxyz[buf][ki];
                 }
                 sx = cxyz.x;
                 sy = cxyz.y;
@@ -522,6 +544,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
             }
         }
         if (CLUSTER) cluster_sync(); else __syncthreads();
+        if (CLUSTER && s_abort) break;   // every CTA of an aborted cluster times out in turn
     }
     if (COUNTERS) {
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[0]), cn.tests);
@@ -531,6 +554,73 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[4]), cn.upd);
         if (t == 0 && rank == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[5]), cn.iter);
     }
+}
+
+// The per-iteration synchronisation floor of k_sample: the same selection
+// tail (warp argmax, CTA slots or DSMEM push, one __syncthreads or one
+// barrier.cluster, slot reduction) with no record work.  `sink` receives a
+// value that depends on every round so the loop cannot be elided.
+template <int NT, bool CLUSTER>
+__global__ void __launch_bounds__(NT, 1) k_sync_floor(int64_t iters, unsigned long long* sink, uint32_t* status)
+{
+    constexpr int NW = NT / 32;
+    constexpr int NSLOT = CLUSTER ? kMaxCluster * NW : 1;
+    __shared__ unsigned long long s_wkey[2][NW];
+    __shared__ unsigned long long s_ckey[2][NSLOT];
+    __shared__ float4 s_cxyz[2][NSLOT];
+    __shared__ unsigned long long s_mbar[2];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const uint32_t rank = CLUSTER ? cluster_ctarank() : 0u;
+    const uint32_t C = CLUSTER ? cluster_nctarank() : 1u;
+    if (CLUSTER && t == 0) {
+        mbar_init(&s_mbar[0], 1);
+        mbar_init(&s_mbar[1], 1);
+        fence_mbar_init_cluster();
+    }
+    if (CLUSTER) cluster_sync();
+    unsigned long long acc = 0ull;
+    unsigned long long pk = make_key(static_cast<float>(t), blockIdx.x * NT + t);
+    float sx = 0.f;
+    bool ok = true;
+    for (int64_t j = 1; j < iters && ok; ++j) {
+        const int par = static_cast<int>(j & 1);
+        pk = (pk ^ static_cast<unsigned long long>(j)) + static_cast<unsigned long long>(__float_as_uint(sx) & 1u);
+        unsigned long long wk, gbest;
+        warp_argmax_lane(pk, &wk);
+        if (!CLUSTER) {
+            if (lane == 0) s_wkey[par][w] = wk;
+            __syncthreads();
+            const unsigned long long ck = lane < NW ? s_wkey[par][lane] : 0ull;
+            warp_argmax_lane(ck, &gbest);
+        } else {
+            const uint32_t buf = static_cast<uint32_t>(j - 1) & 1u, ph = (static_cast<uint32_t>(j - 1) >> 1) & 1u;
+            if (t == 0) mbar_arrive_expect_tx(&s_mbar[buf], 24u * C * NW);
+            if (lane < static_cast<int>(C)) {
+                const uint32_t rb = map_shared(&s_mbar[buf], lane);
+                st_async_u64(map_shared(&s_ckey[buf][rank * NW + w], lane), wk, rb);
+                st_async_f32x4(map_shared(&s_cxyz[buf][rank * NW + w], lane), make_float4(sx, sx, sx, 0.f), rb);
+            }
+            if (!mbar_wait_bounded(&s_mbar[buf], ph, kSpinLimit)) {
+                atomicCAS(status, 0u, kStatusTimeout);
+                ok = false;
+            }
+            unsigned long long kk = 0ull;
+            uint32_t ki = 0;
+            for (uint32_t q = lane; q < C * NW; q += 32) {
+                const unsigned long long x = s_ckey[buf][q];
+                if (x > kk) {
+                    kk = x;
+                    ki = q;
+                }
+            }
+            const int gl = warp_argmax_lane(kk, &gbest);
+            ki = __shfl_sync(0xffffffffu, ki, gl);
+            sx = s_cxyz[buf][ki].x + 1.0f;
+        }
+        acc += gbest;
+    }
+    if (CLUSTER) cluster_sync();
+    if (t == 0) sink[blockIdx.x] = acc;
 }
 
 template <int NT, bool CLUSTER, bool COUNTERS>
@@ -593,6 +683,32 @@ cudaError_t launch_nt(const SampleArgs& args, int NT, int C, int64_t n_clouds, c
                      : launch_one<512, CLUSTER, COUNTERS>(args, C, n_clouds, st);
 }
 
+template <int NT, bool CLUSTER>
+cudaError_t launch_floor(int C, int64_t iters, unsigned long long* sink, cudaStream_t st)
+{
+    auto kern = k_sync_floor<NT, CLUSTER>;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.blockDim = dim3(NT);
+    cfg.gridDim = dim3(CLUSTER ? C : 1);
+    cfg.stream = st;
+    if (CLUSTER) {
+        if (C > 8) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+        }
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, iters, sink, reinterpret_cast<uint32_t*>(sink + 16));
+    note_launches(1);
+    return e;
+}
+
 }  // namespace
 
 cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int64_t* out, const rfps_opts& o,
@@ -625,6 +741,12 @@ cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int6
     }
     return cl ? launch_nt<true, false>(a, o.threads, C, n_clouds, st)
               : launch_nt<false, false>(a, o.threads, C, n_clouds, st);
+}
+
+cudaError_t launch_sync_floor(int C, int NT, int64_t iters, unsigned long long* sink, cudaStream_t st)
+{
+    if (C > 1) return NT == 256 ? launch_floor<256, true>(C, iters, sink, st) : launch_floor<512, true>(C, iters, sink, st);
+    return NT == 256 ? launch_floor<256, false>(1, iters, sink, st) : launch_floor<512, false>(1, iters, sink, st);
 }
 
 }  // namespace rfps
