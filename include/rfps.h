@@ -134,6 +134,26 @@ rfps_status rfps_fps_host(const float *host_points, int64_t n, int64_t m,
                           int64_t start, int64_t *host_out, const rfps_opts *opts,
                           void *workspace, size_t workspace_bytes, void *stream);
 
+/* rfps_fps_noalloc: rfps_fps for callers that cannot allocate device memory
+ * on their own path (a real-time loop that cannot afford an allocation's
+ * implicit synchronisation and latency, a plug-in inside an application
+ * whose allocator owns the device, code running while the device heap is
+ * reserved).  The paper has no counterpart: it is an interface choice of this
+ * library.  The scratch is a 64 MiB array compiled into librfps.so; each GPU
+ * that loads the library holds it until the process exits.  The call takes
+ * only the input and output buffers (same meaning as rfps_fps) and calls no
+ * allocating routine.  N whose rfps_fps workspace exceeds 64 MiB (with
+ * default options, N above 725,440 points) is rejected with RFPS_ENOMEM.  Every call on a GPU
+ * shares the one array: calls whose work overlaps on the GPU race, so
+ * serialise them (one stream, or events).  The kernels reset the state they
+ * need at the start of each call.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) and should come before any
+ * stream capture.  Device-side errors (a non-finite coordinate) are not
+ * reported by this call; the output is then unspecified. */
+rfps_status rfps_fps_noalloc(const float *points, int64_t n, int64_t m,
+                             int64_t start, int64_t *out_idx,
+                             const rfps_opts *opts, void *stream);
+
 /* ------------------------------------------------------------------------
  * Ragged batch: B clouds concatenated in one point array, sampled by one
  * persistent launch whose CTA clusters take clouds from a device work queue

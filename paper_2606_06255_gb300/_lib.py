@@ -70,6 +70,7 @@ def _load():
         "rfps_fps": (st, [vp, i64, i64, i64, vp, optp, vp, sz, vp]),
         "rfps_fps_host_workspace_size": (sz, [i64, optp]),
         "rfps_fps_host": (st, [vp, i64, i64, i64, vp, optp, vp, sz, vp]),
+        "rfps_fps_noalloc": (st, [vp, i64, i64, i64, vp, optp, vp]),
         "rfps_batch_workspace_size": (sz, [i64, i64, i64, optp]),
         "rfps_fps_batched": (st, [vp, i64, vp, i64, vp, vp, i64, vp, optp, vp, sz, vp]),
         "rfps_plain_workspace_size": (sz, [i64, i64]),
