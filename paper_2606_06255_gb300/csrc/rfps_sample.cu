@@ -506,11 +506,14 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     cr = __shfl_sync(0xffffffffu, cr, cl);
                     if (gbest != 0ull) cxyz = fast ? v.best[cr] : v.get_best(cr);
                 } else {
-                    // every warp pushes its best (key, xyz) into slot [rank][warp] of every CTA with
-                    // st.async; each CTA's barrier for this round expects C * NW * 24 bytes
+                    // Every warp pushes its best (key, xyz) by st.async into slot [rank][warp] of every
+                    // CTA; each CTA's barrier for this round expects C * NW * 24 bytes.  (Reducing in the
+                    // CTA first and pushing one candidate per CTA has a lower isolated floor at 16 CTAs
+                    // but adds a CTA barrier after the record work, and measured slower in the kernel.)
                     const uint32_t buf = it & 1u, ph = (it >> 1) & 1u;
                     ++it;
-                    if (t == 0) mbar_arrive_expect_tx(&s_mbar[buf], 24u * C * NW);
+                    const uint32_t nslot = C * NW;
+                    if (t == 0) mbar_arrive_expect_tx(&s_mbar[buf], 24u * nslot);
                     float4 wxyz = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (wk != 0ull && lane < static_cast<int>(C)) wxyz = fast ? v.best[wr] : v.get_best(wr);
                     if (lane < static_cast<int>(C)) {
@@ -524,7 +527,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     }
                     unsigned long long kk = 0ull;
                     uint32_t ki = 0;
-                    for (uint32_t q = lane; q < C * NW; q += 32) {
+                    for (uint32_t q = lane; q < nslot; q += 32) {
                         const unsigned long long x = s_ckey[buf][q];
                         if (x > kk) {
                             kk = x;
@@ -581,8 +584,7 @@ __global__ void __launch_bounds__(NT, 1) k_sync_floor(int64_t iters, unsigned lo
     unsigned long long acc = 0ull;
     unsigned long long pk = make_key(static_cast<float>(t), blockIdx.x * NT + t);
     float sx = 0.f;
-    bool ok = true;
-    for (int64_t j = 1; j < iters && ok; ++j) {
+    for (int64_t j = 1; j < iters; ++j) {   // a timed-out wait is recorded; every round stays bounded
         const int par = static_cast<int>(j & 1);
         pk = (pk ^ static_cast<unsigned long long>(j)) + static_cast<unsigned long long>(__float_as_uint(sx) & 1u);
         unsigned long long wk, gbest;
@@ -594,19 +596,17 @@ __global__ void __launch_bounds__(NT, 1) k_sync_floor(int64_t iters, unsigned lo
             warp_argmax_lane(ck, &gbest);
         } else {
             const uint32_t buf = static_cast<uint32_t>(j - 1) & 1u, ph = (static_cast<uint32_t>(j - 1) >> 1) & 1u;
-            if (t == 0) mbar_arrive_expect_tx(&s_mbar[buf], 24u * C * NW);
+            const uint32_t nslot = C * NW;
+            if (t == 0) mbar_arrive_expect_tx(&s_mbar[buf], 24u * nslot);
             if (lane < static_cast<int>(C)) {
                 const uint32_t rb = map_shared(&s_mbar[buf], lane);
                 st_async_u64(map_shared(&s_ckey[buf][rank * NW + w], lane), wk, rb);
                 st_async_f32x4(map_shared(&s_cxyz[buf][rank * NW + w], lane), make_float4(sx, sx, sx, 0.f), rb);
             }
-            if (!mbar_wait_bounded(&s_mbar[buf], ph, kSpinLimit)) {
-                atomicCAS(status, 0u, kStatusTimeout);
-                ok = false;
-            }
+            if (!mbar_wait_bounded(&s_mbar[buf], ph, kSpinLimit)) atomicCAS(status, 0u, kStatusTimeout);
             unsigned long long kk = 0ull;
             uint32_t ki = 0;
-            for (uint32_t q = lane; q < C * NW; q += 32) {
+            for (uint32_t q = lane; q < nslot; q += 32) {
                 const unsigned long long x = s_ckey[buf][q];
                 if (x > kk) {
                     kk = x;
