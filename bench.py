@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--opts", default="", help="JSON dict of rfps_opts overrides")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--floor-sweep", action="store_true",
+                    help="print the sampling loop's per-iteration synchronisation floor for every launch shape")
+    ap.add_argument("--once", action="store_true",
+                    help="run the path once on the workload and exit (the case profiled with ncu)")
     return ap.parse_args()
 
 
@@ -202,6 +206,13 @@ def main():
     import paper_2606_06255_gb300 as rf
 
     torch.cuda.set_device(local)
+    if args.floor_sweep:
+        for cluster in (1, 2, 4, 8, 16):
+            for threads in (256, 512):
+                ms = min(rf.sync_floor(cluster, threads, 25000) for _ in range(3))
+                print(json.dumps({"cluster": cluster, "threads": threads, "ns_per_iteration": ms * 1e6 / 24999}),
+                      flush=True)
+        return 0
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
@@ -216,6 +227,14 @@ def main():
 
     def step():
         rf.fps(pts, m, start, opts=opts, workspace=ws, out=out)
+
+    if args.once:
+        step()
+        torch.cuda.synchronize()
+        if rf.status(ws) != 0:
+            raise RuntimeError("device status %d" % rf.status(ws))
+        print(json.dumps({"once": args.workload, "n": n, "m": m, "first": out[:4].tolist()}), flush=True)
+        return 0
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -278,26 +297,32 @@ def main():
     peak, peak_kind = load_peaks()
     achieved = alg_bytes / (k_ms / 1e3) / 1e9
 
-    # ---- plain GPU FPS on the same cloud (best plain variant for the size)
+    # ---- per-iteration synchronisation floor of the launch shape the step used
+    rs = rf.resolved_opts(n, opts)
+    floor_ms = min(rf.sync_floor(rs["cluster"], rs["threads"], max(2, m)) for _ in range(3))
+    floor_ns = floor_ms * 1e6 / max(1, m - 1)
+
+    # ---- plain GPU FPS on the same cloud: cluster-resident (variant 1) and whole-GPU (variant 2)
     plain = None
     if not args.no_plain:
-        variant = 2 if n > 200000 else 1
+        plain = {}
         pws = torch.empty(rf.plain_workspace_size(n), dtype=torch.uint8, device=dev)
-        rf.plain_fps(pts, m, start, variant=variant, workspace=pws, out=out)
-        torch.cuda.synchronize()
-        p_ms = []
-        for _ in range(max(2, min(args.steps, 5))):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+        for variant, label in ((1, "cluster"), (2, "whole_gpu")):
             rf.plain_fps(pts, m, start, variant=variant, workspace=pws, out=out)
-            e1.record(stream)
             torch.cuda.synchronize()
-            p_ms.append(e0.elapsed_time(e1))
-        pm = statistics.mean(p_ms)
-        plain = {"variant": variant, "ms_per_cloud": pm, "samples_per_s": m / (pm / 1e3),
-                 "radiusfps_speedup": pm / ms_per_step}
+            p_ms = []
+            for _ in range(max(2, min(args.steps, 3))):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rf.plain_fps(pts, m, start, variant=variant, workspace=pws, out=out)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                p_ms.append(e0.elapsed_time(e1))
+            pm = statistics.mean(p_ms)
+            plain[label] = {"variant": variant, "ms_per_cloud": pm, "samples_per_s": m / (pm / 1e3),
+                            "radiusfps_speedup": pm / ms_per_step}
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     host_pts = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
@@ -335,7 +360,9 @@ def main():
                          "frac": achieved / peak, "traffic": ncu_traffic(args.workload),
                          "kernel": "k_sample", "kernel_ms": k_ms, "alg_bytes_per_launch": alg_bytes,
                          "peak_kind": peak_kind,
-                         "ns_per_iteration": k_ms * 1e6 / max(1, m - 1)},
+                         "ns_per_iteration": k_ms * 1e6 / max(1, m - 1),
+                         "sync_floor_ns_per_iteration": floor_ns,
+                         "launch_shape": {"cluster": rs["cluster"], "threads": rs["threads"]}},
             "counters": c,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": n * 12,

@@ -87,6 +87,13 @@ typedef struct {
 /* Fills *opts with the defaults (all automatic, prune = skip = 1). */
 void rfps_opts_default(rfps_opts *opts);
 
+/* The options a call on a cloud of n points will use, automatic fields
+ * resolved (host only, no device work): threads 256, clusters of 16 CTAs
+ * from 2,048 points up (1 below), records of at most 128 points; n_vox stays
+ * 0 when automatic because the device picks it per cloud (about
+ * 0.7 * cbrt(N)).  RFPS_EINVAL for invalid options. */
+rfps_status rfps_opts_resolve(int64_t n, const rfps_opts *in, rfps_opts *out);
+
 /* Human-readable name of a status code (static string, never NULL). */
 const char *rfps_status_str(int status);
 

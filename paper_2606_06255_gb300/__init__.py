@@ -5,6 +5,7 @@ include/rfps.h); this package is its thin Python binding plus the batching,
 autotuning and serving layers around it.
 """
 
+from . import autotune, batch, serve, shard  # noqa: F401
 from ._lib import (  # noqa: F401
     Counters,
     Index,
@@ -21,6 +22,7 @@ from ._lib import (  # noqa: F401
     plain_fps,
     plain_fps_batched,
     plain_workspace_size,
+    resolved_opts,
     status,
     sync_floor,
     workspace_size,

@@ -65,6 +65,7 @@ def _load():
         "rfps_opts_default": (None, [optp]),
         "rfps_status_str": (ctypes.c_char_p, [ctypes.c_int]),
         "rfps_version": (ctypes.c_int, []),
+        "rfps_opts_resolve": (st, [i64, optp, optp]),
         "rfps_launch_count": (i64, []),
         "rfps_fps_workspace_size": (sz, [i64, optp]),
         "rfps_fps": (st, [vp, i64, i64, i64, vp, optp, vp, sz, vp]),
@@ -267,6 +268,13 @@ def sync_floor(cluster: int, threads: int, iterations: int, stream=None) -> floa
     if int(ws[128:132].view(torch.int32).item()) != 0:
         raise RfpsError(ETIMEOUT, "rfps_sync_floor (device)")
     return e0.elapsed_time(e1)
+
+
+def resolved_opts(n: int, opts=None) -> dict:
+    """The launch options the library uses for a cloud of n points (rfps_opts_resolve)."""
+    o = Opts()
+    _check(_lib.rfps_opts_resolve(n, _opts(opts), ctypes.byref(o)), "rfps_opts_resolve")
+    return o.as_dict()
 
 
 def launch_count() -> int:

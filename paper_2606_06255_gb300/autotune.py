@@ -1,0 +1,106 @@
+"""Autotuner for the launch shape: cluster size, CTA threads, record chunk
+(points per warp-sized record) and voxel resolution.
+
+The sampling loop's per-iteration time is the cluster exchange plus the work
+of the unpruned records, and the best trade-off depends on the cloud's size
+and shape (Sec. 5.6.2 reports the same sensitivity to the voxel resolution
+v).  The tuner times each candidate with CUDA events on representative
+clouds (single cloud or a ragged batch) and keeps the fastest.  Results are
+cached in a JSON file keyed by workload class and size bucket.  Every
+candidate returns the same indices, so tuning never changes results.
+"""
+
+from __future__ import annotations
+
+import json
+import math
+import os
+import statistics
+
+import torch
+
+from . import _lib
+
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "_cache",
+                             "autotune.json")
+
+
+def size_bucket(n: int) -> int:
+    return int(round(math.log2(max(1, n))))
+
+
+def key(kind: str, n: int, batch: int = 1) -> str:
+    return f"{kind}:b{batch}:n{size_bucket(n)}"
+
+
+def default_candidates(batch: bool = False):
+    cands = []
+    for cluster in ((2, 4, 8, 16) if batch else (4, 8, 16)):
+        for threads in (256, 512):
+            for chunk in (64, 128):
+                cands.append({"cluster": cluster, "threads": threads, "chunk": chunk})
+    return cands
+
+
+def _time(fn, reps):
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def tune_single(points: torch.Tensor, m: int, start: int = 0, candidates=None, reps: int = 3):
+    """Time each candidate on one cloud; returns (best opts, [(ms, opts), ...])."""
+    n = points.shape[0]
+    out = torch.empty(m, dtype=torch.int64, device=points.device)
+    rows = []
+    for o in candidates or default_candidates(False):
+        ws = torch.empty(_lib.workspace_size(n, o), dtype=torch.uint8, device=points.device)
+        ms = _time(lambda: _lib.fps(points, m, start, opts=o, workspace=ws, out=out), reps)
+        rows.append((ms, o))
+    rows.sort(key=lambda r: r[0])
+    return rows[0][1], rows
+
+
+def tune_batch(points: torch.Tensor, sizes, ms, starts=None, candidates=None, reps: int = 3):
+    """Time each candidate on a ragged batch (one launch); returns (best opts, table)."""
+    meta = _lib._batch_meta(sizes, ms, starts, points.device)
+    rows = []
+    for o in candidates or default_candidates(True):
+        ws = torch.empty(_lib.batch_workspace_size(points.shape[0], len(sizes), max(sizes), o), dtype=torch.uint8,
+                         device=points.device)
+        t = _time(lambda: _lib.fps_batched(points, sizes, ms, starts, opts=o, workspace=ws, meta=meta), reps)
+        rows.append((t, o))
+    rows.sort(key=lambda r: r[0])
+    return rows[0][1], rows
+
+
+def load_cache(path: str = DEFAULT_CACHE) -> dict:
+    if not os.path.exists(path):
+        return {}
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def save(entry_key: str, opts: dict, table, path: str = DEFAULT_CACHE):
+    cache = load_cache(path)
+    cache[entry_key] = {"opts": opts, "table": [{"ms": round(ms, 4), "opts": o} for ms, o in table]}
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    with open(path, "w") as fh:
+        json.dump(cache, fh, indent=1, sort_keys=True)
+
+
+def best_opts(kind: str, n: int, batch: int = 1, path: str = DEFAULT_CACHE):
+    """Cached best options for this workload class and size bucket, or None (library defaults)."""
+    e = load_cache(path).get(key(kind, n, batch))
+    return dict(e["opts"]) if e else None

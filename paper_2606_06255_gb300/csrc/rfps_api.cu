@@ -160,6 +160,21 @@ struct rfps_index {
     int sorted_buf;
 };
 
+static rfps_status check_opts(const rfps_opts* o)
+{
+    if (!o) return RFPS_OK;
+    if (o->n_vox < 0 || o->n_vox > kMaxNVox) return RFPS_EINVAL;
+    if (o->cluster != 0 && o->cluster != 1 && o->cluster != 2 && o->cluster != 4 && o->cluster != 8 &&
+        o->cluster != 16)
+        return RFPS_EINVAL;
+    if (o->threads != 0 && o->threads != 256 && o->threads != 512) return RFPS_EINVAL;
+    if (o->chunk != 0 && (!is_pow2(o->chunk) || o->chunk < 32 || o->chunk > 4096)) return RFPS_EINVAL;
+    if (o->radius_mode != 0 && o->radius_mode != 1) return RFPS_EINVAL;
+    return RFPS_OK;
+}
+
+static bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
+
 extern "C" {
 
 void rfps_opts_default(rfps_opts* o)
@@ -187,22 +202,18 @@ const char* rfps_status_str(int s)
 
 int rfps_version(void) { return 1; }
 
-int64_t rfps_launch_count(void) { return g_launches.load(); }
-
-static rfps_status check_opts(const rfps_opts* o)
+rfps_status rfps_opts_resolve(int64_t n, const rfps_opts* in, rfps_opts* out)
 {
-    if (!o) return RFPS_OK;
-    if (o->n_vox < 0 || o->n_vox > kMaxNVox) return RFPS_EINVAL;
-    if (o->cluster != 0 && o->cluster != 1 && o->cluster != 2 && o->cluster != 4 && o->cluster != 8 &&
-        o->cluster != 16)
-        return RFPS_EINVAL;
-    if (o->threads != 0 && o->threads != 256 && o->threads != 512) return RFPS_EINVAL;
-    if (o->chunk != 0 && (!is_pow2(o->chunk) || o->chunk < 32 || o->chunk > 4096)) return RFPS_EINVAL;
-    if (o->radius_mode != 0 && o->radius_mode != 1) return RFPS_EINVAL;
+    if (!out || n < 1) return RFPS_EINVAL;
+    const rfps_status s = check_opts(in);
+    if (s != RFPS_OK) return s;
+    *out = resolve_opts(in, n);
     return RFPS_OK;
 }
 
-static bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
+int64_t rfps_launch_count(void) { return g_launches.load(); }
+
+
 
 size_t rfps_fps_workspace_size(int64_t n, const rfps_opts* opts)
 {

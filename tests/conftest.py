@@ -14,6 +14,9 @@ if HERE not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: takes more than a few seconds")
+    # test modules import the package, which loads librfps.so: build it first if needed
+    import __graft_entry__
+    __graft_entry__._builder().build()
 
 
 def pytest_collection_modifyitems(config, items):

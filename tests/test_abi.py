@@ -48,6 +48,16 @@ def test_defaults(lib):
     assert d["n_vox"] == 0 and d["cluster"] == 0 and d["threads"] == 0 and d["chunk"] == 0
 
 
+def test_resolved_defaults(lib):
+    import paper_2606_06255_gb300 as rf
+    small, big = rf.resolved_opts(1000), rf.resolved_opts(100000)
+    assert small["cluster"] == 1 and big["cluster"] == 16
+    assert big["threads"] == 256 and big["chunk"] == 128 and big["prune"] == 1 and big["skip"] == 1
+    assert rf.resolved_opts(100000, {"cluster": 4, "threads": 512})["cluster"] == 4
+    with pytest.raises(rf.RfpsError):
+        rf.resolved_opts(100, {"chunk": 3})
+
+
 def test_workspace_sizes_are_host_only(lib):
     from paper_2606_06255_gb300 import Opts
     s1 = lib.rfps_fps_workspace_size(1000, None)

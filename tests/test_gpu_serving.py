@@ -1,0 +1,79 @@
+"""Batching, CUDA-graph replay, autotuning and serving on the GPU."""
+
+import numpy as np
+import pytest
+import torch
+
+import cloudgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rf():
+    import paper_2606_06255_gb300 as rf
+    return rf
+
+
+def _mixed(n, seed):
+    rng = np.random.default_rng(seed)
+    clouds = []
+    for b in range(n):
+        size = int(rng.integers(3000, 40000))
+        pts = cloudgen.room_cloud(size, seed=seed + b) if b % 2 == 0 else cloudgen.lidar_cloud(size, seed=seed + b)
+        clouds.append(pts)
+    return clouds
+
+
+def test_serving_results_identical_alone_and_in_the_mix(rf):
+    clouds = _mixed(14, 700)
+    rng = np.random.default_rng(1)
+    t = np.cumsum(rng.exponential(1.0 / 2000.0, size=len(clouds)))
+    reqs = [rf.serve.Request(i, float(t[i]), c, max(1, c.shape[0] // 8), i % 5) for i, c in enumerate(clouds)]
+    ex = rf.serve.GpuExecutor(n_slots=3, opts={"cluster": 4})
+    rep = rf.serve.Server(ex, mem_budget=1 << 30, max_inflight=3, max_batch=4).run(reqs)
+    assert len(rep.completed) == len(reqs) and not rep.rejected
+    by_id = {c.rid: c for c in rep.completed}
+    for r in reqs:
+        alone = rf.fps(torch.from_numpy(r.points).cuda(), r.m, r.start, check=True).cpu().numpy()
+        np.testing.assert_array_equal(by_id[r.rid].indices, alone)
+        if r.rid < 4:
+            np.testing.assert_array_equal(alone, oracle.fps(r.points, r.m, r.start, threads=0))
+    s = rep.summary()
+    assert s["p99_latency_ms"] >= s["p50_latency_ms"] > 0
+    assert rep.max_inflight_batches >= 2      # batches overlapped on the device
+
+
+def test_graph_replayed_batch(rf):
+    clouds = _mixed(6, 900)
+    sizes = [c.shape[0] for c in clouds]
+    ms = [n // 4 for n in sizes]
+    bs = rf.batch.BatchSampler(sizes, ms, opts={"cluster": 2})
+    bs.load(clouds)
+    out1 = bs.split(bs.run().clone())
+    out2 = bs.split(bs.run())
+    assert bs.status() == 0
+    for b, c in enumerate(clouds):
+        ref = oracle.fps(c, ms[b], 0, threads=0)
+        np.testing.assert_array_equal(out1[b], ref)
+        np.testing.assert_array_equal(out2[b], ref)
+    # a new batch of the same shape through the same graph
+    other = [cloudgen.uniform_cloud(n, seed=77 + i) for i, n in enumerate(sizes)]
+    bs.load(other)
+    out3 = bs.split(bs.run())
+    for b, c in enumerate(other):
+        np.testing.assert_array_equal(out3[b], oracle.fps(c, ms[b], 0, threads=0))
+
+
+def test_autotune_picks_a_candidate_with_identical_results(rf, tmp_path):
+    pts_np = cloudgen.room_cloud(20000, seed=5)
+    pts = torch.from_numpy(pts_np).cuda()
+    cands = [{"cluster": 2, "threads": 256}, {"cluster": 8, "threads": 256, "chunk": 64}]
+    best, table = rf.autotune.tune_single(pts, 4000, 0, candidates=cands, reps=1)
+    assert best in cands and len(table) == 2
+    path = str(tmp_path / "tune.json")
+    rf.autotune.save(rf.autotune.key("room", 20000), best, table, path=path)
+    assert rf.autotune.best_opts("room", 20000, path=path) == best
+    got = rf.fps(pts, 4000, 0, opts=best, check=True).cpu().numpy()
+    np.testing.assert_array_equal(got, oracle.fps(pts_np, 4000, 0, threads=0))

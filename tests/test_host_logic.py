@@ -1,0 +1,147 @@
+"""Host-side logic without a GPU: serving scheduler (simulated executor) and
+multi-rank sharding (world size 2 over gloo)."""
+
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import cloudgen
+import oracle
+
+from paper_2606_06255_gb300 import serve, shard
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += max(dt, 1e-5)
+
+
+class SimExecutor:
+    """Runs the oracle on launch and completes after a simulated duration."""
+
+    def __init__(self, clock, per_sample_s=1e-6, bytes_per_point=100):
+        self.clock = clock
+        self.per_sample = per_sample_s
+        self.bpp = bytes_per_point
+        self.launched = []
+
+    def mem_needed(self, batch):
+        return sum(r.points.shape[0] for r in batch) * self.bpp
+
+    def launch(self, batch, slot):
+        self.launched.append([r.rid for r in batch])
+        res = [oracle.fps(r.points, r.m, r.start) for r in batch]
+        dur = max(r.m for r in batch) * self.per_sample
+        return {"t_done": self.clock() + dur, "res": res}
+
+    def done(self, h):
+        return self.clock() >= h["t_done"]
+
+    def results(self, h):
+        return h["res"]
+
+
+def _requests(n, rate, seed=0):
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    reqs = []
+    for i in range(n):
+        pts = cloudgen.uniform_cloud(int(rng.integers(200, 2000)), seed=100 + i)
+        reqs.append(serve.Request(i, float(t[i]), pts, max(1, pts.shape[0] // 8), int(rng.integers(0, 10))))
+    return reqs
+
+
+def test_scheduler_completes_everything_with_exact_results():
+    clk = FakeClock()
+    ex = SimExecutor(clk)
+    reqs = _requests(40, rate=2000.0)
+    rep = serve.Server(ex, mem_budget=400_000, max_inflight=3, max_batch=4).run(reqs, clock=clk, sleep=clk.sleep)
+    assert len(rep.completed) == 40 and not rep.rejected
+    by_id = {c.rid: c for c in rep.completed}
+    for r in reqs:
+        c = by_id[r.rid]
+        np.testing.assert_array_equal(c.indices, oracle.fps(r.points, r.m, r.start))
+        assert c.admitted >= r.arrival and c.finished >= c.admitted
+    s = rep.summary()
+    assert s["p99_latency_ms"] >= s["p50_latency_ms"] > 0
+    assert rep.max_inflight_batches <= 3
+    assert rep.peak_mem <= 400_000
+    assert max(len(b) for b in ex.launched) <= 4
+    # continuous batching: later arrivals were admitted while earlier batches ran
+    assert rep.max_inflight_batches >= 2
+
+
+def test_scheduler_admits_by_memory_and_rejects_oversize():
+    clk = FakeClock()
+    ex = SimExecutor(clk, bytes_per_point=1000)
+    reqs = _requests(10, rate=5000.0, seed=3)
+    big = serve.Request(99, 0.0005, cloudgen.uniform_cloud(5000, seed=7), 10)
+    rep = serve.Server(ex, mem_budget=2_500_000, max_inflight=4, max_batch=8).run(reqs + [big], clock=clk,
+                                                                                 sleep=clk.sleep)
+    assert rep.rejected == [99]
+    assert len(rep.completed) == 10
+    assert rep.peak_mem <= 2_500_000
+
+
+def test_assignment_balances_and_covers():
+    sizes = [8000, 200000, 50000, 12000, 90000, 30000, 150000, 9000]
+    ms = [n // 4 for n in sizes]
+    shards = shard.assign(sizes, ms, 3)
+    flat = sorted(b for s in shards for b in s)
+    assert flat == list(range(len(sizes)))
+    assert shard.assign(sizes, ms, 3) == shards          # deterministic
+    loads = [sum(sizes[b] * ms[b] for b in s) for s in shards]
+    assert max(loads) <= sum(loads) / 3 + max(n * m for n, m in zip(sizes, ms))
+    assert shard.assign(sizes, ms, 1) == [list(range(len(sizes)))]
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, sizes, ms, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    clouds = [cloudgen.uniform_cloud(n, seed=500 + b) for b, n in enumerate(sizes)]
+    mine = shard.my_clouds(sizes, ms, world, rank)
+    local = {b: oracle.fps(clouds[b], ms[b], 0).tolist() for b in mine}
+    gathered = [None] * world
+    dist.all_gather_object(gathered, local)
+    if rank == 0:
+        merged = {}
+        for g in gathered:
+            merged.update(g)
+        q.put(merged)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_over_gloo_shard_without_collectives_on_data():
+    sizes = [300, 1200, 700, 2000, 150, 900]
+    ms = [max(1, n // 4) for n in sizes]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, sizes, ms, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    merged = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert sorted(merged) == list(range(len(sizes)))
+    for b, n in enumerate(sizes):
+        assert merged[b] == oracle.fps(cloudgen.uniform_cloud(n, seed=500 + b), ms[b], 0).tolist()
