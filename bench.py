@@ -44,7 +44,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="room100k", choices=["room100k", "uniform4k", "lidar1m"])
+    ap.add_argument("--workload", default="room100k",
+                    choices=["room100k", "uniform4k", "lidar1m", "batch64", "serving"])
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: offered clouds per second")
+    ap.add_argument("--requests", type=int, default=600, help="serving: timed requests")
     ap.add_argument("--opts", default="", help="JSON dict of rfps_opts overrides")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -193,6 +196,83 @@ def run_reference(args, rank):
     return 0
 
 
+def _events(torch, fn, reps, flush):
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def run_batch64(args, rf, torch):
+    """64 ragged clouds: one graph-replayed batched launch vs 64 per-cloud launches vs plain batched."""
+    import cloudgen
+    clouds, desc = cloudgen.workload("batch64")
+    sizes = [c.points.shape[0] for c in clouds]
+    ms = [c.m for c in clouds]
+    opts = json.loads(args.opts) if args.opts else {"cluster": 8}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    bs = rf.batch.BatchSampler(sizes, ms, opts=opts)
+    bs.load([c.points for c in clouds])
+    for _ in range(max(args.warmup, 3)):
+        bs.run()
+    torch.cuda.synchronize()
+    l0 = rf.launch_count()
+    t_batch = _events(torch, bs.run, args.steps, flush)
+    launches = (rf.launch_count() - l0) // args.steps
+    ref = bs.out.cpu().numpy()
+    cat, off = bs.points, bs.offsets
+    views = [cat[int(off[b]):int(off[b + 1])] for b in range(len(sizes))]
+    wss = [torch.empty(rf.workspace_size(sizes[b], opts), dtype=torch.uint8, device="cuda") for b in range(len(sizes))]
+    outs = [torch.empty(ms[b], dtype=torch.int64, device="cuda") for b in range(len(sizes))]
+
+    def per_cloud():
+        for b in range(len(sizes)):
+            rf.fps(views[b], ms[b], 0, opts=opts, workspace=wss[b], out=outs[b])
+    per_cloud()
+    t_sep = _events(torch, per_cloud, 2, flush)
+    same = bool(np.array_equal(np.concatenate([o.cpu().numpy() for o in outs]), ref))
+    plain = {}
+    pws = torch.empty(rf.plain_workspace_size(cat.shape[0], len(sizes)), dtype=torch.uint8, device="cuda")
+    for v in (1, 0):
+        res = {}
+        t = _events(torch, lambda: res.setdefault("o", rf.plain_fps_batched(cat, sizes, ms, variant=v, workspace=pws,
+                                                                           meta=bs.meta)[0]), 1, flush)
+        plain[f"variant{v}"] = {"ms": t, "clouds_per_s": len(sizes) / (t / 1e3)}
+    print(json.dumps({
+        "metric": "clouds/s", "value": len(sizes) / (t_batch / 1e3), "unit": "clouds/s", "workload": "batch64",
+        "desc": desc, "clouds": len(sizes), "points": int(sum(sizes)), "samples": int(sum(ms)),
+        "ms_per_batch": t_batch, "samples_per_s": sum(ms) / (t_batch / 1e3), "opts": opts, "graph": True,
+        "gpu_launches_per_batch": launches,
+        "per_cloud_launches": {"ms": t_sep, "clouds_per_s": len(sizes) / (t_sep / 1e3), "same_indices": same},
+        "batched_vs_per_cloud": t_sep / t_batch, "plain_batched": plain}), flush=True)
+    return 0
+
+
+def run_serving(args, rf):
+    """Poisson request stream through the continuous-batching server."""
+    from paper_2606_06255_gb300 import serve
+    opts = json.loads(args.opts) if args.opts else {"cluster": 4}
+    reqs = serve.poisson_workload(args.requests + 16, args.rate)
+    ex = serve.GpuExecutor(8, opts=opts)
+    srv = serve.Server(ex, mem_budget=48 << 30, max_inflight=8, max_batch=8)
+    srv.run(reqs[:16])
+    t0 = reqs[16].arrival
+    rep = srv.run([serve.Request(r.rid, r.arrival - t0, r.points, r.m, r.start) for r in reqs[16:]])
+    out = rep.summary()
+    out.update({"metric": "p99 latency / clouds/s", "workload": "serving", "offered_rate": args.rate,
+                "requests": args.requests, "opts": opts, "slots": 8, "max_batch": 8,
+                "sizes": "N log-uniform [20000, 1200000], M = N/8, half room / half LiDAR"})
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -213,6 +293,10 @@ def main():
                 print(json.dumps({"cluster": cluster, "threads": threads, "ns_per_iteration": ms * 1e6 / 24999}),
                       flush=True)
         return 0
+    if args.workload == "batch64":
+        return run_batch64(args, rf, torch)
+    if args.workload == "serving":
+        return run_serving(args, rf)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
@@ -307,11 +391,11 @@ def main():
     if not args.no_plain:
         plain = {}
         pws = torch.empty(rf.plain_workspace_size(n), dtype=torch.uint8, device=dev)
-        for variant, label in ((1, "cluster"), (2, "whole_gpu")):
+        for variant, label in ((1, "cluster"), (2, "whole_gpu"), (0, "one_cta_per_cloud")):
             rf.plain_fps(pts, m, start, variant=variant, workspace=pws, out=out)
             torch.cuda.synchronize()
             p_ms = []
-            for _ in range(max(2, min(args.steps, 3))):
+            for _ in range(1 if variant == 0 else max(2, min(args.steps, 3))):
                 flush.zero_()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
