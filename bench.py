@@ -223,9 +223,8 @@ def run_batch64(args, rf, torch):
     for _ in range(max(args.warmup, 3)):
         bs.run()
     torch.cuda.synchronize()
-    l0 = rf.launch_count()
     t_batch = _events(torch, bs.run, args.steps, flush)
-    launches = (rf.launch_count() - l0) // args.steps
+    launches = bs.kernels_per_run
     ref = bs.out.cpu().numpy()
     cat, off = bs.points, bs.offsets
     views = [cat[int(off[b]):int(off[b + 1])] for b in range(len(sizes))]

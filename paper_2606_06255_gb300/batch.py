@@ -36,6 +36,7 @@ class BatchSampler:
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.out = torch.empty(int(self.out_offsets[-1]), dtype=torch.int64, device=self.device)
         self._graph = None
+        self.kernels_per_run = None
         if graph:
             self._capture()
 
@@ -53,8 +54,10 @@ class BatchSampler:
             self._launch(s)          # first call outside capture: kernel attributes, device check
         s.synchronize()
         g = torch.cuda.CUDAGraph()
+        before = _lib.launch_count()
         with torch.cuda.graph(g, stream=s):
             self._launch(s)
+        self.kernels_per_run = _lib.launch_count() - before   # kernel nodes each replay launches
         torch.cuda.current_stream(self.device).wait_stream(s)
         self._graph = g
 
