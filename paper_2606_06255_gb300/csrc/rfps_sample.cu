@@ -54,10 +54,11 @@ struct SampleArgs {
     int64_t* out;
     size_t smem_bytes;         // dynamic shared memory per CTA
     int prune, skip;
-    int resident;              // 1: keep a CTA's points in shared memory when they fit
+    int resident;              // 1: keep records' points in shared memory while they fit
 };
 
 constexpr int kMaxCluster = 16;
+constexpr uint32_t kResident = 0x80000000u;   // rng.x flag: the record's points are in shared memory
 constexpr uint32_t kSpinLimit = 1u << 22;   // try_wait rounds before a wait gives up
 
 // Shared-memory record state of one CTA: ct = (centre, prune threshold),
@@ -279,32 +280,37 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     v.rng[l] = rg;
                     mine += rg.y;
                 }
-                uint32_t total;
-                block_exclusive_sum<NT>(mine, s_scr, &total);
-                resident = a.resident && total <= P;
-                if (resident) {
-                    // shared-memory offsets of my records: contiguous chunks per thread, then a block scan
+                (void)mine;
+                __syncthreads();   // every record's range is in shared memory before the chunked scan reads it
+                if (a.resident && P > 0) {
+                    // Records are made resident in order while their points fit: shared-memory
+                    // offsets from a block scan of the counts (contiguous chunks per thread); a
+                    // resident record's rng.x becomes kResident | offset in the CTA's point array.
                     const uint32_t per = (nloc + NT - 1) / NT;
                     const uint32_t l0 = min(nloc, t * per), l1 = min(nloc, l0 + per);
                     uint32_t sum = 0;
                     for (uint32_t l = l0; l < l1; ++l) sum += v.rng[l].y;
+                    uint32_t total;
                     uint32_t off = block_exclusive_sum<NT>(sum, s_scr, &total);
                     for (uint32_t l = l0; l < l1; ++l) {
                         const uint32_t cnt = v.rng[l].y;
-                        s_wl[l] = off;       // staging: the worklist is not in use yet
+                        s_wl[l] = (off + cnt <= P) ? off : 0xffffffffu;   // staging: worklist not in use yet
                         off += cnt;
                     }
                     __syncthreads();
                     for (uint32_t l = w; l < nloc; l += NW) {
                         const uint2 rg = v.rng[l];
                         const uint32_t so = s_wl[l];
+                        if (so == 0xffffffffu) continue;
                         for (uint32_t q = lane; q < rg.y; q += 32) {
                             s_pts[so + q] = a.pts4[rg.x + q];
                             s_orig[so + q] = a.porig[rg.x + q];
                         }
                     }
                     __syncthreads();
-                    for (uint32_t l = t; l < nloc; l += NT) v.rng[l].x = s_wl[l];
+                    for (uint32_t l = t; l < nloc; l += NT)
+                        if (s_wl[l] != 0xffffffffu) v.rng[l].x = kResident | s_wl[l];
+                    resident = true;
                 }
             } else {
                 v.nsm = static_cast<uint32_t>(a.smem_bytes / 48);
@@ -404,11 +410,12 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         const uint32_t l = s_wl[i];
                         const uint2 rg = v.rng[l];
                         float bx = 0.f, by = 0.f, bz = 0.f;
+                        const bool in_smem = resident && (rg.x & kResident);
                         const unsigned long long lk =
-                            resident ? visit_points<PPL, COUNTERS>(s_pts, s_orig, rg.x, rg.y, first, a.skip, sx, sy,
-                                                                   sz, lane, bx, by, bz, cn)
-                                     : visit_points<PPL, COUNTERS>(a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx,
-                                                                   sy, sz, lane, bx, by, bz, cn);
+                            in_smem ? visit_points<PPL, COUNTERS>(s_pts, s_orig, rg.x & ~kResident, rg.y, first,
+                                                                  a.skip, sx, sy, sz, lane, bx, by, bz, cn)
+                                    : visit_points<PPL, COUNTERS>(a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx,
+                                                                  sy, sz, lane, bx, by, bz, cn);
                         unsigned long long rk;
                         const int wl = warp_argmax_lane(lk, &rk);
                         const float wx = __shfl_sync(0xffffffffu, bx, wl);
