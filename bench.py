@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--floor-sweep", action="store_true",
                     help="print the sampling loop's per-iteration synchronisation floor for every launch shape")
+    ap.add_argument("--study", choices=["m-sweep", "ablation", "nvox"],
+                    help="latency / memory vs M, prune-skip ablation, or voxel-resolution sensitivity on --workload")
     ap.add_argument("--once", action="store_true",
                     help="run the path once on the workload and exit (the case profiled with ncu)")
     return ap.parse_args()
@@ -210,6 +212,51 @@ def _events(torch, fn, reps, flush):
     return statistics.median(ts)
 
 
+def run_study(args, rf, torch, cloud, pts, opts):
+    """Secondary studies on one cloud (each row: RadiusFPS vs the plain baselines, same GB300)."""
+    n = cloud.points.shape[0]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    base = dict(opts or {})
+
+    def t_fps(m, o, reps=3):
+        ws = torch.empty(rf.workspace_size(n, o), dtype=torch.uint8, device="cuda")
+        out = torch.empty(m, dtype=torch.int64, device="cuda")
+        rf.fps(pts, m, 0, opts=o, workspace=ws, out=out)
+        return _events(torch, lambda: rf.fps(pts, m, 0, opts=o, workspace=ws, out=out), reps, flush), ws.numel()
+
+    def t_plain(m, v, reps=2):
+        ws = torch.empty(rf.plain_workspace_size(n), dtype=torch.uint8, device="cuda")
+        out = torch.empty(m, dtype=torch.int64, device="cuda")
+        rf.plain_fps(pts, m, 0, variant=v, workspace=ws, out=out)
+        return _events(torch, lambda: rf.plain_fps(pts, m, 0, variant=v, workspace=ws, out=out), reps, flush)
+
+    rows = []
+    if args.study == "m-sweep":
+        for frac in (1 / 64, 1 / 32, 1 / 16, 1 / 8, 1 / 4):
+            m = max(1, int(n * frac))
+            ms, wsb = t_fps(m, base or None)
+            best_plain = min(t_plain(m, 1), t_plain(m, 2))
+            rows.append({"m": m, "ms": ms, "mpts_per_s": n / ms / 1e3, "workspace_mb": wsb / 2**20,
+                         "input_mb": n * 12 / 2**20, "plain_best_ms": best_plain, "speedup": best_plain / ms})
+    elif args.study == "ablation":
+        m = cloud.m
+        for prune, skip in ((1, 1), (1, 0), (0, 1), (0, 0)):
+            o = dict(base, prune=prune, skip=skip)
+            ms, _ = t_fps(m, o)
+            cws = torch.empty(rf.workspace_size(n, dict(o, counters=1)), dtype=torch.uint8, device="cuda")
+            rf.fps(pts, m, 0, opts=dict(o, counters=1), workspace=cws)
+            rows.append({"prune": prune, "skip": skip, "ms": ms, "counters": rf.counters(cws)})
+        rows.append({"plain_cluster_ms": t_plain(m, 1), "plain_whole_gpu_ms": t_plain(m, 2)})
+    else:
+        m = cloud.m
+        for nv in (8, 12, 16, 24, 32, 48, 64, 96):
+            ms, _ = t_fps(m, dict(base, n_vox=nv))
+            rows.append({"n_vox": nv, "ms": ms})
+    print(json.dumps({"study": args.study, "workload": args.workload, "n": n, "opts": base or "default",
+                      "rows": rows}), flush=True)
+    return 0
+
+
 def run_batch64(args, rf, torch):
     """64 ragged clouds: one graph-replayed batched launch vs 64 per-cloud launches vs plain batched."""
     import cloudgen
@@ -310,6 +357,9 @@ def main():
 
     def step():
         rf.fps(pts, m, start, opts=opts, workspace=ws, out=out)
+
+    if args.study:
+        return run_study(args, rf, torch, cloud, pts, opts)
 
     if args.once:
         step()
