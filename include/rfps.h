@@ -244,7 +244,8 @@ rfps_status rfps_counters_read(const void *workspace, rfps_counters *out,
  *   rfps_index_build   copies nothing from the caller after it returns: the
  *                      index holds the sorted points it needs.  Allocates
  *                      device memory (cudaMallocAsync on `stream`).
- *   rfps_index_sample  M samples from the index (same contract as rfps_fps).
+ *   rfps_index_sample  M samples from the index (same contract as rfps_fps);
+ *                      starts a new sequence and keeps its state on the device.
  *   rfps_index_bytes   device bytes the index holds.
  *   rfps_index_free    releases the index (stream-ordered on the stream it was
  *                      built on); NULL is ignored.
@@ -261,6 +262,17 @@ rfps_status rfps_index_build(const float *points, int64_t n,
                              void *stream);
 rfps_status rfps_index_sample(rfps_index *index, int64_t m, int64_t start,
                               int64_t *out_idx, void *stream);
+/* rfps_index_sample_more: incremental sampling.  Continues the sequence of the
+ * last rfps_index_sample / rfps_index_sample_more call on this index and
+ * writes the next m_more indices (device, int64) to out_idx.  The FPS state
+ * stays on the device between calls: every point's distance to the samples so
+ * far, each voxel record's Dist_v key, best point and prune threshold, and
+ * the last sample, whose update Alg. 1 applies before the next selection.  The
+ * result equals the corresponding slice of rfps_fps with M = (samples so far)
+ * + m_more.  RFPS_EINVAL without a prior rfps_index_sample, or if the total
+ * would exceed N.  One sequence per index at a time (stream-ordered). */
+rfps_status rfps_index_sample_more(rfps_index *index, int64_t m_more,
+                                   int64_t *out_idx, void *stream);
 size_t rfps_index_bytes(const rfps_index *index);
 void rfps_index_free(rfps_index *index);
 rfps_status rfps_index_export(const rfps_index *index, int64_t *n_records,

@@ -82,6 +82,7 @@ def _load():
         "rfps_counters_read": (st, [vp, ctypes.POINTER(Counters), vp]),
         "rfps_index_build": (st, [vp, i64, optp, ctypes.POINTER(vp), vp]),
         "rfps_index_sample": (st, [vp, i64, i64, vp, vp]),
+        "rfps_index_sample_more": (st, [vp, i64, vp, vp]),
         "rfps_index_bytes": (sz, [vp]),
         "rfps_index_free": (None, [vp]),
         "rfps_index_export": (st, [vp, ctypes.POINTER(i64), vp, vp, vp, vp, vp, vp, ctypes.POINTER(i32)]),
@@ -303,6 +304,16 @@ class Index:
         if out is None:
             out = torch.empty(m, dtype=torch.int64, device=self.device)
         _check(_lib.rfps_index_sample(self._h, m, start, out.data_ptr(), _stream(stream)), "rfps_index_sample")
+        return out
+
+    def sample_more(self, m_more: int, stream=None, out: torch.Tensor | None = None) -> torch.Tensor:
+        """The next m_more samples of the sequence started by the last sample() call."""
+        if self._h is None:
+            raise RuntimeError("index freed")
+        if out is None:
+            out = torch.empty(m_more, dtype=torch.int64, device=self.device)
+        _check(_lib.rfps_index_sample_more(self._h, m_more, out.data_ptr(), _stream(stream)),
+               "rfps_index_sample_more")
         return out
 
     def export(self) -> dict:

@@ -34,7 +34,7 @@ int nvox_cap(int64_t n_clouds)
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
-__global__ void k_rearm(WsHeader* hdr, CloudDev* clouds, int64_t m, int64_t start)
+__global__ void k_rearm(WsHeader* hdr, CloudDev* clouds, int64_t m, int64_t start, uint32_t resume)
 {
     hdr->status = 0;
     hdr->work = 0;
@@ -42,6 +42,7 @@ __global__ void k_rearm(WsHeader* hdr, CloudDev* clouds, int64_t m, int64_t star
     clouds[0].m = m;
     clouds[0].start = start;
     clouds[0].out_off = 0;
+    clouds[0].resume = resume;
 }
 
 rfps_status from_cuda(cudaError_t e) { return e == cudaSuccess ? RFPS_OK : RFPS_ECUDA; }
@@ -158,6 +159,7 @@ struct rfps_index {
     int64_t n;
     cudaStream_t stream;
     int sorted_buf;
+    int64_t taken;   // samples of the current sequence so far (0: no saved state)
 };
 
 static rfps_status check_opts(const rfps_opts* o)
@@ -405,6 +407,7 @@ rfps_status rfps_index_build(const float* points, int64_t n, const rfps_opts* op
     ix->n = n;
     ix->stream = static_cast<cudaStream_t>(stream);
     ix->sorted_buf = static_cast<int>(ix->L.radix_passes & 1);
+    ix->taken = 0;
     ix->bytes = ix->L.total;
     if (cudaMallocAsync(&ix->mem, ix->bytes, ix->stream) != cudaSuccess) {
         delete ix;
@@ -430,12 +433,33 @@ rfps_status rfps_index_sample(rfps_index* ix, int64_t m, int64_t start, int64_t*
     char* ws = static_cast<char*>(ix->mem);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     k_rearm<<<1, 1, 0, st>>>(reinterpret_cast<WsHeader*>(ws + ix->L.header),
-                             reinterpret_cast<CloudDev*>(ws + ix->L.clouds), m, start);
+                             reinterpret_cast<CloudDev*>(ws + ix->L.clouds), m, start, 0u);
     note_launches(1);
     cudaError_t e = cudaGetLastError();
     const float* own = reinterpret_cast<const float*>(ws + ix->L.host_points);
-    if (e == cudaSuccess) e = launch_sample(ws, ix->L, own, out_idx, ix->o, 1, ix->n, st);
+    if (e == cudaSuccess) e = launch_sample(ws, ix->L, own, out_idx, ix->o, 1, ix->n, st, true);
+    ix->taken = e == cudaSuccess ? m : 0;
     return from_cuda(e);
+}
+
+rfps_status rfps_index_sample_more(rfps_index* ix, int64_t m_more, int64_t* out_idx, void* stream)
+{
+    if (!ix || !out_idx || m_more < 1 || ix->taken < 1 || ix->taken + m_more > ix->n) return RFPS_EINVAL;
+    char* ws = static_cast<char*>(ix->mem);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // m_more iterations, each applying the pending sample's update and selecting the next one
+    k_rearm<<<1, 1, 0, st>>>(reinterpret_cast<WsHeader*>(ws + ix->L.header),
+                             reinterpret_cast<CloudDev*>(ws + ix->L.clouds), m_more + 1, 0, 1u);
+    note_launches(1);
+    cudaError_t e = cudaGetLastError();
+    const float* own = reinterpret_cast<const float*>(ws + ix->L.host_points);
+    if (e == cudaSuccess) e = launch_sample(ws, ix->L, own, out_idx, ix->o, 1, ix->n, st, true);
+    if (e != cudaSuccess) {
+        ix->taken = 0;
+        return RFPS_ECUDA;
+    }
+    ix->taken += m_more;
+    return RFPS_OK;
 }
 
 size_t rfps_index_bytes(const rfps_index* ix) { return ix ? ix->bytes : 0; }

@@ -89,7 +89,9 @@ __global__ void k_setup(WsHeader* hdr, CloudDev* clouds, uint32_t* order, const 
                 c.bbox[3 + a] = 0u;        // running max
             }
             c.valid = ok ? 1u : 0u;
-            c.pad = 0;
+            c.resume = 0;
+            c.last[0] = c.last[1] = c.last[2] = 0.0f;
+            c.pad2 = 0;
             cells = static_cast<uint32_t>(nv) * static_cast<uint32_t>(nv) * static_cast<uint32_t>(nv);
             if (!ok) atomicOr(&s_bad, 1u);
             clouds[b] = c;

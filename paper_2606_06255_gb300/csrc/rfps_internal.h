@@ -25,7 +25,9 @@ struct CloudDev {
     uint32_t cell_base;// first global cell id of the cloud
     uint32_t bbox[6];  // order-preserving encodings of min xyz / max xyz during the reduction
     uint32_t valid;    // 1 if the cloud passed the device-side checks
-    uint32_t pad;
+    uint32_t resume;   // 1: continue a saved sampling state instead of starting from `start`
+    float last[3];     // coordinates of the last selected sample (saved state)
+    uint32_t pad2;
 };
 static_assert(sizeof(CloudDev) % 8 == 0, "CloudDev alignment");
 
@@ -72,7 +74,8 @@ cudaError_t launch_build(char* ws, const WsLayout& L, const float* points, const
                          int64_t max_n, cudaStream_t st);
 // Persistent sampling launch over the clouds of ws.
 cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int64_t* out,
-                          const rfps_opts& o, int64_t n_clouds, int64_t max_n, cudaStream_t st);
+                          const rfps_opts& o, int64_t n_clouds, int64_t max_n, cudaStream_t st,
+                          bool save_state = false);
 // Synchronisation floor of the sampling loop (same tail, no record work).
 cudaError_t launch_sync_floor(int C, int NT, int64_t iters, unsigned long long* sink, cudaStream_t st);
 // Plain FPS launches.

@@ -40,7 +40,7 @@ namespace {
 
 struct SampleArgs {
     WsHeader* hdr;
-    const CloudDev* clouds;
+    CloudDev* clouds;
     const uint32_t* order;
     int64_t n_clouds;
     const float* pts;          // caller's AoS points
@@ -55,6 +55,7 @@ struct SampleArgs {
     size_t smem_bytes;         // dynamic shared memory per CTA
     int prune, skip;
     int resident;              // 1: keep records' points in shared memory while they fit
+    int save_state;            // 1: write the sampling state back at the end (resumable index)
 };
 
 constexpr int kMaxCluster = 16;
@@ -242,8 +243,10 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
         if (CLUSTER) cluster_sync(); else __syncthreads();
         const uint32_t item = s_item;
         if (item >= a.n_clouds) break;
-        const CloudDev c = a.clouds[a.order[item]];
+        const uint32_t cloud = a.order[item];
+        const CloudDev c = a.clouds[cloud];
         if (c.valid) {
+            const bool resume = c.resume != 0;
             const uint32_t K = c.rec_end - c.rec_off;
             const uint32_t nloc = K > rank ? (K - rank + C - 1) / C : 0u;
             const uint32_t gbase = c.rec_off + rank;
@@ -274,9 +277,15 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     const uint32_t k = v.g(l);
                     const float4 sph = a.rec_sph[k];
                     const uint2 rg = a.rec_rng[k];
-                    v.ct[l] = make_float4(sph.x, sph.y, sph.z, nan);
-                    v.best[l] = make_float4(0.f, 0.f, 0.f, sph.w);
-                    v.key[l] = 0ull;
+                    if (resume) {   // saved state: threshold, best point (radius in .w), key
+                        v.ct[l] = make_float4(sph.x, sph.y, sph.z, a.rec_thr[k]);
+                        v.best[l] = a.rec_best[k];
+                        v.key[l] = a.rec_key[k];
+                    } else {
+                        v.ct[l] = make_float4(sph.x, sph.y, sph.z, nan);
+                        v.best[l] = make_float4(0.f, 0.f, 0.f, sph.w);
+                        v.key[l] = 0ull;
+                    }
                     v.rng[l] = rg;
                     mine += rg.y;
                 }
@@ -323,24 +332,33 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     const uint32_t k = v.g(l);
                     const float4 sph = a.rec_sph[k];
                     if (l < v.nsm) {
-                        v.ct[l] = make_float4(sph.x, sph.y, sph.z, nan);
-                        v.best[l] = make_float4(0.f, 0.f, 0.f, sph.w);
-                        v.key[l] = 0ull;
+                        if (resume) {
+                            v.ct[l] = make_float4(sph.x, sph.y, sph.z, a.rec_thr[k]);
+                            v.best[l] = a.rec_best[k];
+                            v.key[l] = a.rec_key[k];
+                        } else {
+                            v.ct[l] = make_float4(sph.x, sph.y, sph.z, nan);
+                            v.best[l] = make_float4(0.f, 0.f, 0.f, sph.w);
+                            v.key[l] = 0ull;
+                        }
                         v.rng[l] = a.rec_rng[k];
-                    } else {
+                    } else if (!resume) {
                         a.rec_thr[k] = nan;
                         a.rec_best[k] = make_float4(0.f, 0.f, 0.f, sph.w);
                         a.rec_key[k] = 0ull;
                     }
                 }
             }
+            // the sample whose update comes first: the start point, or the saved last sample
             const int64_t g0 = c.pt_off + c.start;
-            float sx = a.pts[3 * g0 + 0], sy = a.pts[3 * g0 + 1], sz = a.pts[3 * g0 + 2];
+            float sx = resume ? c.last[0] : a.pts[3 * g0 + 0];
+            float sy = resume ? c.last[1] : a.pts[3 * g0 + 1];
+            float sz = resume ? c.last[2] : a.pts[3 * g0 + 2];
             if (t == 0) {
                 s_wlc[0] = 0;   // every CTA's own worklist counters
                 s_wlc[1] = 0;
             }
-            if (rank == 0 && t == 0) a.out[c.out_off] = c.start;
+            if (rank == 0 && t == 0 && !resume) a.out[c.out_off] = c.start;
             // this lane's cached max over the records it owns (my, my + NT, ...)
             unsigned long long lkey = 0ull;
             uint32_t lrec = 0xffffffffu;
@@ -348,7 +366,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
             __syncthreads();
 
             for (int64_t j = 1; j < c.m; ++j) {
-                const bool first = (j == 1);
+                const bool first = (j == 1) && !resume;   // the initial update of Sec. 3.3
                 const int par = static_cast<int>(j & 1);
                 unsigned long long pk;   // this lane's partial max (key, record) for the selection
                 uint32_t prec;
@@ -549,8 +567,41 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                 sy = cxyz.y;
                 sz = cxyz.z;
                 if (rank == 0 && t == 0)
-                    a.out[c.out_off + j] = static_cast<int64_t>(key_index(gbest)) - c.pt_off;
+                    a.out[c.out_off + (resume ? j - 1 : j)] = static_cast<int64_t>(key_index(gbest)) - c.pt_off;
                 if (COUNTERS) ++cn.iter;
+            }
+            if (a.save_state) {
+                // state for a later resume: records kept in shared memory, resident points'
+                // distances, and the last selected sample (every CTA holds the same one)
+                __syncthreads();
+                if (fast) {
+                    for (uint32_t l = t; l < nloc; l += NT) {
+                        const uint32_t k = v.g(l);
+                        a.rec_key[k] = v.key[l];
+                        a.rec_best[k] = v.best[l];
+                        a.rec_thr[k] = v.ct[l].w;
+                    }
+                    if (resident) {
+                        for (uint32_t l = w; l < nloc; l += NW) {
+                            const uint2 rg = v.rng[l];
+                            if (!(rg.x & kResident)) continue;
+                            const uint32_t go = a.rec_rng[v.g(l)].x, so = rg.x & ~kResident;
+                            for (uint32_t q = lane; q < rg.y; q += 32) a.pts4[go + q].w = s_pts[so + q].w;
+                        }
+                    }
+                } else {
+                    for (uint32_t l = t; l < v.nsm; l += NT) {
+                        const uint32_t k = v.g(l);
+                        a.rec_key[k] = v.key[l];
+                        a.rec_best[k] = v.best[l];
+                        a.rec_thr[k] = v.ct[l].w;
+                    }
+                }
+                if (rank == 0 && t == 0) {
+                    a.clouds[cloud].last[0] = sx;
+                    a.clouds[cloud].last[1] = sy;
+                    a.clouds[cloud].last[2] = sz;
+                }
             }
         }
         if (CLUSTER) cluster_sync(); else __syncthreads();
@@ -719,12 +770,12 @@ cudaError_t launch_floor(int C, int64_t iters, unsigned long long* sink, cudaStr
 }  // namespace
 
 cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int64_t* out, const rfps_opts& o,
-                          int64_t n_clouds, int64_t max_n, cudaStream_t st)
+                          int64_t n_clouds, int64_t max_n, cudaStream_t st, bool save_state)
 {
     (void)max_n;
     SampleArgs a;
     a.hdr = reinterpret_cast<WsHeader*>(ws + L.header);
-    a.clouds = reinterpret_cast<const CloudDev*>(ws + L.clouds);
+    a.clouds = reinterpret_cast<CloudDev*>(ws + L.clouds);
     a.order = reinterpret_cast<const uint32_t*>(ws + L.order);
     a.n_clouds = n_clouds;
     a.pts = points;
@@ -740,6 +791,7 @@ cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int6
     a.skip = o.skip;
     a.smem_bytes = 0;   // set per instantiation from the device's opt-in limit
     a.resident = 1;
+    a.save_state = save_state ? 1 : 0;
     const int C = o.cluster;
     const bool cl = C > 1;
     if (o.counters) {

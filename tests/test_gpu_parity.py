@@ -241,3 +241,31 @@ def test_launch_counter_moves(rf):
     before = rf.launch_count()
     gpu_fps(rf, cloudgen.uniform_cloud(500, seed=1), 50)
     assert rf.launch_count() > before
+
+
+@pytest.mark.parametrize("opts", [None, {"cluster": 1, "chunk": 32}, {"cluster": 4}, {"cluster": 1, "n_vox": 40, "chunk": 32}])
+def test_incremental_sampling_continues_the_sequence(rf, opts):
+    """sample(m1) then sample_more(m2), sample_more(m3) equals one FPS run of m1 + m2 + m3 samples."""
+    pts = cloudgen.room_cloud(40000, seed=51)
+    ref = oracle.fps(pts, 9000, 3, threads=0)
+    ix = rf.Index(dev(pts), opts=opts)
+    a = ix.sample(2000, 3).cpu().numpy()
+    b = ix.sample_more(1).cpu().numpy()
+    c = ix.sample_more(6999).cpu().numpy()
+    np.testing.assert_array_equal(np.concatenate([a, b, c]), ref)
+    # a new sequence on the same index
+    np.testing.assert_array_equal(ix.sample(500, 0).cpu().numpy(), oracle.fps(pts, 500, 0, threads=0))
+    np.testing.assert_array_equal(ix.sample_more(100).cpu().numpy(), oracle.fps(pts, 600, 0, threads=0)[500:])
+    with pytest.raises(rf.RfpsError):
+        ix.sample_more(40000)
+    ix.free()
+
+
+def test_incremental_sampling_with_records_in_global_memory(rf):
+    """Resume where most voxel records live in global memory (one CTA, fine voxels, tiny records)."""
+    pts = cloudgen.uniform_cloud(60000, seed=52)
+    ref = oracle.fps(pts, 3000, 0, threads=0)
+    ix = rf.Index(dev(pts), opts={"cluster": 1, "n_vox": 40, "chunk": 32})
+    got = [ix.sample(1000, 0).cpu().numpy(), ix.sample_more(1500).cpu().numpy(), ix.sample_more(500).cpu().numpy()]
+    np.testing.assert_array_equal(np.concatenate(got), ref)
+    ix.free()
