@@ -28,7 +28,7 @@ int auto_nvox_bound(int64_t n, int cap)
 int nvox_cap(int64_t n_clouds)
 {
     int cap = kMaxNVox;
-    while (cap > 1 && static_cast<double>(cap) * cap * cap * static_cast<double>(n_clouds) >= 4294967295.0) --cap;
+    while (cap > 1 && std::ldexp(1.0, 3 * morton_bits(cap)) * static_cast<double>(n_clouds) >= 4294967295.0) --cap;
     return cap;
 }
 
@@ -117,7 +117,7 @@ WsLayout make_layout(int64_t total_n, int64_t n_clouds, int64_t max_n, const rfp
     // sort key bits: global cell ids < n_clouds * n_vox_max^3
     const int cap = nvox_cap(n_clouds);
     const int nv = o.n_vox > 0 ? std::min(o.n_vox, cap) : auto_nvox_bound(max_n, cap);
-    const double cells = static_cast<double>(nv) * nv * nv * static_cast<double>(n_clouds);
+    const double cells = std::ldexp(1.0, 3 * morton_bits(nv)) * static_cast<double>(n_clouds);
     int bits = 1;
     while (bits < 32 && std::ldexp(1.0, bits) < cells) ++bits;
     L.radix_passes = (bits + kRadixBits - 1) / kRadixBits;
@@ -499,7 +499,11 @@ rfps_status rfps_index_export(const rfps_index* ix, int64_t* n_records, uint32_t
         s = RFPS_ECUDA;
     if (s == RFPS_OK) {
         for (int64_t r = 0; r < R; ++r) {
-            if (voxel_id) voxel_id[r] = keys[rng[r].x] - c.cell_base;
+            if (voxel_id) {
+                const uint32_t code = keys[rng[r].x] - c.cell_base;   // Morton code -> v_z n^2 + v_y n + v_x
+                const uint32_t n = static_cast<uint32_t>(c.n_vox);
+                voxel_id[r] = (morton_compact(code >> 2) * n + morton_compact(code >> 1)) * n + morton_compact(code);
+            }
             if (first) first[r] = rng[r].x;
             if (count) count[r] = rng[r].y;
         }

@@ -6,7 +6,8 @@
 //                cloud, global cell numbering, largest-first cloud order
 //   k_bbox       bounding box per cloud + non-finite detection        (Alg. 2 l.1)
 //   k_grid       L = alpha * max(E) / n_vox  (Eq. voxel_size)          (Alg. 2 l.2)
-//   k_bin        clamped floor binning, voxel id v_z n^2 + v_y n + v_x (Alg. 2 Phase 1)
+//   k_bin        clamped floor binning (Alg. 2 Phase 1); the sort key is the cell's Morton
+//                code rather than v_z n^2 + v_y n + v_x, so sorted neighbours are 3-D compact
 //   radix sort   stable LSD sort of (global cell id, point index)      (Alg. 2 sort)
 //   records      active voxels, split into records of <= chunk points,
 //                with offset / count (Phase 3), centre c_k, a radius that
@@ -92,7 +93,7 @@ __global__ void k_setup(WsHeader* hdr, CloudDev* clouds, uint32_t* order, const 
             c.resume = 0;
             c.last[0] = c.last[1] = c.last[2] = 0.0f;
             c.pad2 = 0;
-            cells = static_cast<uint32_t>(nv) * static_cast<uint32_t>(nv) * static_cast<uint32_t>(nv);
+            cells = 1u << (3 * morton_bits(nv));   // Morton-ordered cell ids of this cloud
             if (!ok) atomicOr(&s_bad, 1u);
             clouds[b] = c;
         }
@@ -221,7 +222,8 @@ __device__ __forceinline__ uint32_t bin_coord(float p, float mn, float L, int n_
     return static_cast<uint32_t>(f);
 }
 
-// Phase 1: voxel id per point; sort key = cell_base + voxel id, value = point row.
+// Phase 1: voxel coordinates per point; sort key = cell_base + Morton code of the cell,
+// value = point row.
 __global__ void __launch_bounds__(kBoxNT) k_bin(const WsHeader* hdr, const CloudDev* clouds, const float* pts,
                                                 int64_t n_clouds, uint32_t* keys, uint32_t* vals)
 {
@@ -235,7 +237,8 @@ __global__ void __launch_bounds__(kBoxNT) k_bin(const WsHeader* hdr, const Cloud
             const uint32_t vx = bin_coord(p[3 * i + 0], c.gmin[0], c.L, c.n_vox);
             const uint32_t vy = bin_coord(p[3 * i + 1], c.gmin[1], c.L, c.n_vox);
             const uint32_t vz = bin_coord(p[3 * i + 2], c.gmin[2], c.L, c.n_vox);
-            keys[c.pt_off + i] = c.cell_base + (vz * nv + vy) * nv + vx;
+            keys[c.pt_off + i] = c.cell_base + morton3(vx, vy, vz);
+            (void)nv;
             vals[c.pt_off + i] = static_cast<uint32_t>(c.pt_off + i);
         }
     }
@@ -497,9 +500,8 @@ __global__ void k_records(const WsHeader* hdr, const CloudDev* clouds, int64_t n
             else hi = mid - 1;
         }
         const CloudDev c = clouds[lo];
-        const uint32_t nv = static_cast<uint32_t>(c.n_vox);
-        const uint32_t vid = skeys[off] - c.cell_base;
-        const uint32_t v[3] = {vid % nv, (vid / nv) % nv, vid / (nv * nv)};
+        const uint32_t code = skeys[off] - c.cell_base;   // Morton code of the cell
+        const uint32_t v[3] = {morton_compact(code), morton_compact(code >> 1), morton_compact(code >> 2)};
         float cen[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
@@ -540,7 +542,7 @@ cudaError_t launch_setup(char* ws, const WsLayout& L, const int64_t* offsets, co
     const int sort_clouds = (offsets != nullptr && n_clouds > 1 && n_clouds <= 8192) ? 1 : 0;
     // cap n_vox so that the global cell ids of all clouds fit 32 bits
     int cap = kMaxNVox;
-    while (cap > 1 && static_cast<double>(cap) * cap * cap * static_cast<double>(n_clouds) >= 4294967295.0) --cap;
+    while (cap > 1 && std::ldexp(1.0, 3 * morton_bits(cap)) * static_cast<double>(n_clouds) >= 4294967295.0) --cap;
     k_setup<<<1, 256, 0, st>>>(hdr, clouds, order, offsets, out_offsets, starts, n_clouds, total_n, n, m, start,
                                max_n, o.n_vox, cap, 0.7f, sort_clouds);
     note_launches(1);

@@ -18,6 +18,7 @@ constexpr uint32_t kStatusOk = 0;
 constexpr uint32_t kStatusInval = 1;
 constexpr uint32_t kStatusNonFinite = 2;
 constexpr uint32_t kStatusTimeout = 5;
+constexpr uint32_t kStatusUnsupported = 6;
 
 // Canonical FP32 squared distance between p and s.
 __device__ __forceinline__ float sq_dist(float px, float py, float pz, float sx, float sy, float sz)

@@ -91,4 +91,36 @@ void note_launches(int64_t k);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Cells are numbered in Morton (Z) order so that records that are consecutive
+// in sort order are compact in space (the hierarchical path groups 32 of
+// them).  With b = ceil(log2 n_vox) bits per axis a cloud spans 8^b cell ids.
+__host__ __device__ inline int morton_bits(int n_vox)
+{
+    int b = 0;
+    while ((1 << b) < n_vox) ++b;
+    return b;
+}
+__host__ __device__ inline uint32_t morton_spread(uint32_t v)   // 10 bits -> every third bit
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+__host__ __device__ inline uint32_t morton_compact(uint32_t v)
+{
+    v &= 0x09249249u;
+    v = (v | (v >> 2)) & 0x030c30c3u;
+    v = (v | (v >> 4)) & 0x0300f00fu;
+    v = (v | (v >> 8)) & 0x030000ffu;
+    v = (v | (v >> 16)) & 0x3ffu;
+    return v;
+}
+__host__ __device__ inline uint32_t morton3(uint32_t x, uint32_t y, uint32_t z)
+{
+    return morton_spread(x) | (morton_spread(y) << 1) | (morton_spread(z) << 2);
+}
+
 }  // namespace rfps

@@ -62,49 +62,17 @@ constexpr int kMaxCluster = 16;
 constexpr uint32_t kResident = 0x80000000u;   // rng.x flag: the record's points are in shared memory
 constexpr uint32_t kSpinLimit = 1u << 22;   // try_wait rounds before a wait gives up
 
-// Shared-memory record state of one CTA: ct = (centre, prune threshold),
-// best = (best point, covering radius), key = Dist_v key, rng = point range.
+// Shared-memory record state of one CTA (fast path): ct = (centre, prune
+// threshold), best = (best point, covering radius), key = Dist_v key, rng =
+// point range; local record l is global record gbase + l * C.
 struct RecView {
     float4* ct;
     float4* best;
     unsigned long long* key;
     uint2* rng;
-    uint32_t nsm, gbase, C;
+    uint32_t gbase, C;
     const SampleArgs* a;
-    __device__ __forceinline__ bool smem(uint32_t l) const { return l < nsm; }
     __device__ __forceinline__ uint32_t g(uint32_t l) const { return gbase + l * C; }
-    __device__ __forceinline__ float4 get_ct(uint32_t l) const
-    {
-        if (smem(l)) return ct[l];
-        const float4 s = a->rec_sph[g(l)];
-        return make_float4(s.x, s.y, s.z, a->rec_thr[g(l)]);
-    }
-    __device__ __forceinline__ unsigned long long get_key(uint32_t l) const
-    {
-        return smem(l) ? key[l] : a->rec_key[g(l)];
-    }
-    __device__ __forceinline__ float4 get_best(uint32_t l) const
-    {
-        return smem(l) ? best[l] : a->rec_best[g(l)];
-    }
-    __device__ __forceinline__ uint2 get_rng(uint32_t l) const { return smem(l) ? rng[l] : a->rec_rng[g(l)]; }
-    __device__ __forceinline__ float get_radius(uint32_t l) const
-    {
-        return smem(l) ? best[l].w : a->rec_sph[g(l)].w;
-    }
-    __device__ __forceinline__ void put(uint32_t l, unsigned long long k, float x, float y, float z, float r,
-                                        float thr) const
-    {
-        if (smem(l)) {
-            key[l] = k;
-            best[l] = make_float4(x, y, z, r);
-            ct[l].w = thr;
-        } else {
-            a->rec_key[g(l)] = k;
-            a->rec_best[g(l)] = make_float4(x, y, z, r);
-            a->rec_thr[g(l)] = thr;
-        }
-    }
 };
 
 struct Cnt {
@@ -207,7 +175,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
     __shared__ unsigned long long s_ckey[2][NSLOT];
     __shared__ float4 s_cxyz[2][NSLOT];
     __shared__ uint32_t s_scr[NW + 1];
-    __shared__ uint32_t s_item, s_wlc[2], s_abort;
+    __shared__ uint32_t s_item, s_wlc[2], s_rlc[2], s_rlcut[2], s_abort;
     __shared__ unsigned long long s_mbar[2];
 
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -261,8 +229,14 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
             uint32_t* s_orig = nullptr;
             uint32_t* s_wl = nullptr;
             bool resident = false;
+            // hierarchical path (records in global memory, super-records in shared memory)
+            float4* s_sct = nullptr;             // super centre, prune threshold
+            float4* s_sxyz = nullptr;            // best point of the super, radius in .w
+            unsigned long long* s_skey = nullptr;
+            uint32_t* s_slist = nullptr;         // unpruned super-records of this iteration
+            uint32_t* s_rlist = nullptr;         // unpruned records of this iteration
+            uint32_t G = 0, W = 0;
             if (fast) {
-                v.nsm = nloc;
                 v.ct = reinterpret_cast<float4*>(smem);
                 v.best = v.ct + nloc;
                 v.key = reinterpret_cast<unsigned long long*>(v.best + nloc);
@@ -322,30 +296,76 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     resident = true;
                 }
             } else {
-                v.nsm = static_cast<uint32_t>(a.smem_bytes / 48);
-                if (v.nsm > nloc) v.nsm = nloc;
-                v.ct = reinterpret_cast<float4*>(smem);
-                v.best = v.ct + v.nsm;
-                v.key = reinterpret_cast<unsigned long long*>(v.best + v.nsm);
-                v.rng = reinterpret_cast<uint2*>(v.key + v.nsm);
-                for (uint32_t l = t; l < nloc; l += NT) {
-                    const uint32_t k = v.g(l);
-                    const float4 sph = a.rec_sph[k];
-                    if (l < v.nsm) {
-                        if (resume) {
-                            v.ct[l] = make_float4(sph.x, sph.y, sph.z, a.rec_thr[k]);
-                            v.best[l] = a.rec_best[k];
-                            v.key[l] = a.rec_key[k];
-                        } else {
-                            v.ct[l] = make_float4(sph.x, sph.y, sph.z, nan);
-                            v.best[l] = make_float4(0.f, 0.f, 0.f, sph.w);
-                            v.key[l] = 0ull;
-                        }
-                        v.rng[l] = a.rec_rng[k];
-                    } else if (!resume) {
+                // Hierarchical path: every record stays in global memory; each group of 32
+                // consecutive local records is a super-record with a sphere covering all its
+                // records' spheres, the max of their Dist_v keys and the coordinates of the point
+                // that attains it, kept in shared memory.  Pruning tests super-records first.
+                G = (nloc + 31) / 32;
+                if (static_cast<size_t>(G) * 44 + 16 > a.smem_bytes) {
+                    // more records than one CTA can index (beyond ~150k per CTA): larger clusters
+                    // or records are needed; record the error and skip the cloud uniformly
+                    if (t == 0) atomicCAS(&a.hdr->status, 0u, kStatusUnsupported);
+                    G = 0;
+                }
+                s_sct = reinterpret_cast<float4*>(smem);
+                s_sxyz = s_sct + G;
+                s_skey = reinterpret_cast<unsigned long long*>(s_sxyz + G);
+                s_slist = reinterpret_cast<uint32_t*>(s_skey + G);
+                s_rlist = s_slist + G;
+                const size_t used = static_cast<size_t>(G) * 44;
+                const size_t room = a.smem_bytes > used ? (a.smem_bytes - used) / 4 : 0;
+                W = static_cast<uint32_t>(room < nloc ? room : nloc);
+                if (!resume) {
+                    for (uint32_t l = t; l < nloc; l += NT) {
+                        const uint32_t k = v.g(l);
                         a.rec_thr[k] = nan;
-                        a.rec_best[k] = make_float4(0.f, 0.f, 0.f, sph.w);
                         a.rec_key[k] = 0ull;
+                        a.rec_best[k] = make_float4(0.f, 0.f, 0.f, a.rec_sph[k].w);
+                    }
+                }
+                __syncthreads();
+                for (uint32_t g = w; g < G; g += NW) {
+                    const uint32_t l = g * 32 + lane;
+                    const bool valid = l < nloc;
+                    float4 sph = make_float4(0.f, 0.f, 0.f, 0.f);
+                    unsigned long long kk = 0ull;
+                    if (valid) {
+                        sph = a.rec_sph[v.g(l)];
+                        if (resume) kk = a.rec_key[v.g(l)];
+                    }
+                    // bounding box of the member spheres (rounded outwards), its centre
+                    float lo[3], hi[3], cs[3];
+                    const float cc[3] = {sph.x, sph.y, sph.z};
+#pragma unroll
+                    for (int ax = 0; ax < 3; ++ax) {
+                        lo[ax] = valid ? __fsub_rd(cc[ax], sph.w) : 3.4028234e38f;
+                        hi[ax] = valid ? __fadd_ru(cc[ax], sph.w) : -3.4028234e38f;
+                        for (int o = 16; o > 0; o >>= 1) {
+                            lo[ax] = fminf(lo[ax], __shfl_xor_sync(0xffffffffu, lo[ax], o));
+                            hi[ax] = fmaxf(hi[ax], __shfl_xor_sync(0xffffffffu, hi[ax], o));
+                        }
+                        cs[ax] = __fmul_rn(__fadd_rn(lo[ax], hi[ax]), 0.5f);
+                    }
+                    // radius: max over members of |c_m - c_s| + r_m, every step rounded up
+                    float e = 0.f;
+                    if (valid) {
+                        const float d2 = sq_dist(cc[0], cc[1], cc[2], cs[0], cs[1], cs[2]);
+                        const float dist = __fsqrt_ru(__fadd_ru(__fmul_ru(d2, 0x1.00004p0f), 0x1p-120f));
+                        e = __fadd_ru(dist, sph.w);
+                    }
+                    for (int o = 16; o > 0; o >>= 1) e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, o));
+                    const float srad = fmaxf(__fmul_ru(e, 0x1.00001p0f), 0x1p-50f);
+                    unsigned long long gk;
+                    const int gl = warp_argmax_lane(kk, &gk);
+                    float4 bxyz = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (resume && lane == gl && valid) bxyz = a.rec_best[v.g(l)];
+                    bxyz.x = __shfl_sync(0xffffffffu, bxyz.x, gl);
+                    bxyz.y = __shfl_sync(0xffffffffu, bxyz.y, gl);
+                    bxyz.z = __shfl_sync(0xffffffffu, bxyz.z, gl);
+                    if (lane == 0) {
+                        s_sct[g] = make_float4(cs[0], cs[1], cs[2], resume ? prune_threshold(srad, gk) : nan);
+                        s_sxyz[g] = make_float4(bxyz.x, bxyz.y, bxyz.z, srad);
+                        s_skey[g] = gk;
                     }
                 }
             }
@@ -357,6 +377,10 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
             if (t == 0) {
                 s_wlc[0] = 0;   // every CTA's own worklist counters
                 s_wlc[1] = 0;
+                s_rlc[0] = 0;
+                s_rlc[1] = 0;
+                s_rlcut[0] = W;
+                s_rlcut[1] = W;
             }
             if (rank == 0 && t == 0 && !resume) a.out[c.out_off] = c.start;
             // this lane's cached max over the records it owns (my, my + NT, ...)
@@ -451,66 +475,138 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         }
                     }
                 } else {
-                    if (CLUSTER && __syncthreads_or(s_abort != 0)) break;
-                    // ---- records partly in global memory: each warp visits its lanes' unpruned records
-                    for (uint32_t g0r = 0; g0r < nloc; g0r += 32u * NT) {
-                        uint32_t um = 0;
-#pragma unroll 4
+                    // one warp updates record l (global memory) and refreshes its key, best point
+                    // and prune threshold
+                    auto visit_global = [&](uint32_t l) {
+                        const uint32_t k = v.g(l);
+                        const uint2 rg = a.rec_rng[k];
+                        float bx = 0.f, by = 0.f, bz = 0.f;
+                        const unsigned long long lk = visit_points<PPL, COUNTERS>(
+                            a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx, sy, sz, lane, bx, by, bz, cn);
+                        unsigned long long rk;
+                        const int wl = warp_argmax_lane(lk, &rk);
+                        const float wx = __shfl_sync(0xffffffffu, bx, wl);
+                        const float wy = __shfl_sync(0xffffffffu, by, wl);
+                        const float wz = __shfl_sync(0xffffffffu, bz, wl);
+                        if (lane == 0) {
+                            const float r = a.rec_best[k].w;
+                            a.rec_key[k] = rk;
+                            a.rec_best[k] = make_float4(wx, wy, wz, r);
+                            a.rec_thr[k] = prune_threshold(r, rk);
+                        }
+                    };
+                    // ---- A1: prune test of my super-records; unpruned ones to the super list
+                    for (uint32_t g0s = 0; g0s < G; g0s += 32u * NT) {
+                        uint32_t su = 0;
                         for (int b = 0; b < 32; ++b) {
-                            const uint32_t l = g0r + static_cast<uint32_t>(b) * NT + my;
-                            if (l < nloc) {
-                                const bool keep = first || !a.prune || !prune_by_threshold(v.get_ct(l), sx, sy, sz);
-                                um |= keep ? (1u << b) : 0u;
-                                if (COUNTERS && !first) {
-                                    ++cn.tests;
-                                    cn.pruned += keep ? 0 : 1;
-                                }
+                            const uint32_t g = g0s + static_cast<uint32_t>(b) * NT + my;
+                            if (g >= G) break;
+                            const bool keep = first || !a.prune || !prune_by_threshold(s_sct[g], sx, sy, sz);
+                            su |= keep ? (1u << b) : 0u;
+                            if (COUNTERS && !first) {
+                                ++cn.tests;
+                                cn.pruned += keep ? 0 : 1;
                             }
                         }
-                        uint32_t wm = __reduce_or_sync(0xffffffffu, um);
-                        while (wm) {
-                            const int b = __ffs(wm) - 1;
-                            wm &= wm - 1;
-                            uint32_t mask = __ballot_sync(0xffffffffu, (um >> b) & 1u);
+                        const uint32_t nkeep = __popc(su);
+                        uint32_t incl = nkeep;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                            if (lane >= o) incl += u;
+                        }
+                        const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+                        if (wtot) {
+                            uint32_t base = 0;
+                            if (lane == 31) base = atomicAdd(&s_wlc[par], wtot);
+                            base = __shfl_sync(0xffffffffu, base, 31);
+                            uint32_t pos = base + incl - nkeep;
+                            for (uint32_t mm = su; mm; mm &= mm - 1)
+                                s_slist[pos++] = g0s + static_cast<uint32_t>(__ffs(mm) - 1) * NT + my;
+                        }
+                    }
+                    __syncthreads();
+                    if (CLUSTER && s_abort) break;   // uniform: read after the barrier
+                    if (t == 0) {
+                        s_wlc[par ^ 1] = 0;
+                        s_rlc[par ^ 1] = 0;
+                        s_rlcut[par ^ 1] = W;
+                    }
+                    const uint32_t nsl = s_wlc[par];
+                    // ---- A2: records of the unpruned super-records (one per lane); unpruned ones
+                    // go to the record list, or are visited in place when the list is full
+                    for (uint32_t i = w; i < nsl; i += NW) {
+                        const uint32_t g = s_slist[i];
+                        const uint32_t l = g * 32 + lane;
+                        bool keep = false;
+                        if (l < nloc) {
+                            if (first || !a.prune) {
+                                keep = true;
+                            } else {
+                                const uint32_t k = v.g(l);
+                                const float4 sp = a.rec_sph[k];
+                                keep = !prune_by_threshold(make_float4(sp.x, sp.y, sp.z, a.rec_thr[k]), sx, sy, sz);
+                            }
+                            if (COUNTERS && !first) {
+                                ++cn.tests;
+                                cn.pruned += keep ? 0 : 1;
+                            }
+                        }
+                        uint32_t mask = __ballot_sync(0xffffffffu, keep);
+                        if (!mask) continue;
+                        uint32_t base = 0;
+                        if (lane == 0) base = atomicAdd(&s_rlc[par], static_cast<uint32_t>(__popc(mask)));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (base + __popc(mask) <= W) {
+                            if (keep) s_rlist[base + __popc(mask & ((1u << lane) - 1u))] = l;
+                        } else {
+                            // list full: later appends fail too, so the list holds [0, first failed base)
+                            if (lane == 0) atomicMin(&s_rlcut[par], base);
                             while (mask) {
                                 const int src = __ffs(mask) - 1;
                                 mask &= mask - 1;
-                                const uint32_t lr =
-                                    g0r + static_cast<uint32_t>(b) * NT + static_cast<uint32_t>(src * NW + w);
-                                const uint2 rg = v.get_rng(lr);
-                                float bx = 0.f, by = 0.f, bz = 0.f;
-                                const unsigned long long lk = visit_points<PPL, COUNTERS>(
-                                    a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx, sy, sz, lane, bx, by, bz, cn);
-                                unsigned long long rk;
-                                const int wl = warp_argmax_lane(lk, &rk);
-                                const float wx = __shfl_sync(0xffffffffu, bx, wl);
-                                const float wy = __shfl_sync(0xffffffffu, by, wl);
-                                const float wz = __shfl_sync(0xffffffffu, bz, wl);
-                                if (lane == 0) {
-                                    const float r = v.get_radius(lr);
-                                    v.put(lr, rk, wx, wy, wz, r, prune_threshold(r, rk));
-                                }
-                                // keys only decrease: the owner's cached max needs a rescan only
-                                // if this record held it
-                                if (lane == src && lr == lrec) dirty = true;
+                                visit_global(g * 32 + static_cast<uint32_t>(src));
                             }
                         }
                     }
-                    __syncwarp();
-                    if (dirty) {
-                        lkey = 0ull;
-                        lrec = 0xffffffffu;
-                        for (uint32_t l = my; l < nloc; l += NT) {
-                            const unsigned long long kk = v.get_key(l);
-                            if (kk > lkey) {
-                                lkey = kk;
-                                lrec = l;
-                            }
+                    __syncthreads();
+                    // ---- B: one warp per listed record
+                    const uint32_t nrl = min(min(s_rlc[par], s_rlcut[par]), W);
+                    for (uint32_t i = w; i < nrl; i += NW) visit_global(s_rlist[i]);
+                    __syncthreads();
+                    // ---- C: refresh the unpruned super-records from their records
+                    for (uint32_t i = w; i < nsl; i += NW) {
+                        const uint32_t g = s_slist[i];
+                        const uint32_t l = g * 32 + lane;
+                        unsigned long long kk = 0ull;
+                        float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (l < nloc) {
+                            kk = a.rec_key[v.g(l)];
+                            b4 = a.rec_best[v.g(l)];
+                        }
+                        unsigned long long gk;
+                        const int gl = warp_argmax_lane(kk, &gk);
+                        const float bx = __shfl_sync(0xffffffffu, b4.x, gl);
+                        const float by = __shfl_sync(0xffffffffu, b4.y, gl);
+                        const float bz = __shfl_sync(0xffffffffu, b4.z, gl);
+                        if (lane == 0) {
+                            const float srad = s_sxyz[g].w;
+                            s_skey[g] = gk;
+                            s_sxyz[g] = make_float4(bx, by, bz, srad);
+                            s_sct[g].w = prune_threshold(srad, gk);
                         }
                     }
-                    dirty = false;
-                    pk = lkey;
-                    prec = lrec;
+                    __syncthreads();
+                    // ---- D: my super-records' max
+                    pk = 0ull;
+                    prec = 0xffffffffu;
+                    for (uint32_t g = my; g < G; g += NT) {
+                        const unsigned long long kk = s_skey[g];
+                        if (kk > pk) {
+                            pk = kk;
+                            prec = g;
+                        }
+                    }
                 }
                 // ---- selection: warp -> CTA -> cluster
                 __syncwarp();
@@ -529,7 +625,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     uint32_t cr = lane < NW ? s_wrec[par][lane] : 0xffffffffu;
                     const int cl = warp_argmax_lane(ck, &gbest);
                     cr = __shfl_sync(0xffffffffu, cr, cl);
-                    if (gbest != 0ull) cxyz = fast ? v.best[cr] : v.get_best(cr);
+                    if (gbest != 0ull) cxyz = fast ? v.best[cr] : s_sxyz[cr];
                 } else {
                     // Every warp pushes its best (key, xyz) by st.async into slot [rank][warp] of every
                     // CTA; each CTA's barrier for this round expects C * NW * 24 bytes.  (Reducing in the
@@ -540,7 +636,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     const uint32_t nslot = C * NW;
                     if (t == 0) mbar_arrive_expect_tx(&s_mbar[buf], 24u * nslot);
                     float4 wxyz = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (wk != 0ull && lane < static_cast<int>(C)) wxyz = fast ? v.best[wr] : v.get_best(wr);
+                    if (wk != 0ull && lane < static_cast<int>(C)) wxyz = fast ? v.best[wr] : s_sxyz[wr];
                     if (lane < static_cast<int>(C)) {
                         const uint32_t rb = map_shared(&s_mbar[buf], lane);
                         st_async_u64(map_shared(&s_ckey[buf][rank * NW + w], lane), wk, rb);
@@ -589,14 +685,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             for (uint32_t q = lane; q < rg.y; q += 32) a.pts4[go + q].w = s_pts[so + q].w;
                         }
                     }
-                } else {
-                    for (uint32_t l = t; l < v.nsm; l += NT) {
-                        const uint32_t k = v.g(l);
-                        a.rec_key[k] = v.key[l];
-                        a.rec_best[k] = v.best[l];
-                        a.rec_thr[k] = v.ct[l].w;
-                    }
-                }
+                }   // the hierarchical path keeps its records in global memory throughout
                 if (rank == 0 && t == 0) {
                     a.clouds[cloud].last[0] = sx;
                     a.clouds[cloud].last[1] = sy;

@@ -204,8 +204,13 @@ def test_index_matches_oracle_voxel_grid(rf):
             d = np.sqrt(((pts[members].astype(np.float64) - cen.astype(np.float64)) ** 2).sum(1)).max()
             assert e["sphere"][r, 3] >= d and e["sphere"][r, 3] <= d * (1 + 2 ** -18) + 2 ** -49
         assert np.array_equal(pos_vid, vid[orig])
-        # sorted by (voxel id, original index): stable grouping
-        key = vid[orig].astype(np.int64) * len(pts) + orig
+        # sorted by (Morton code of the voxel, original index): stable grouping in Z order
+        vv = vid[orig].astype(np.int64)
+        vx, vy, vz = vv % n_vox, (vv // n_vox) % n_vox, vv // (n_vox * n_vox)
+        code = np.zeros_like(vv)
+        for bit in range(10):
+            code |= ((vx >> bit) & 1) << (3 * bit) | ((vy >> bit) & 1) << (3 * bit + 1) | ((vz >> bit) & 1) << (3 * bit + 2)
+        key = code * len(pts) + orig
         assert np.all(np.diff(key) > 0)
         ix.free()
 
@@ -269,3 +274,22 @@ def test_incremental_sampling_with_records_in_global_memory(rf):
     got = [ix.sample(1000, 0).cpu().numpy(), ix.sample_more(1500).cpu().numpy(), ix.sample_more(500).cpu().numpy()]
     np.testing.assert_array_equal(np.concatenate(got), ref)
     ix.free()
+
+
+@pytest.mark.parametrize("name,opts", [
+    ("lidar_200k_c1", {"cluster": 1}),
+    ("lidar_200k_c2_nv64", {"cluster": 2, "n_vox": 64}),
+    ("room_150k_c1_chunk32", {"cluster": 1, "chunk": 32, "n_vox": 48}),
+    ("uniform_120k_c1", {"cluster": 1, "n_vox": 64, "chunk": 64, "threads": 512}),
+])
+def test_hierarchical_path_many_records(rf, name, opts):
+    """Clouds whose records exceed one CTA's shared memory: super-record pruning, records in global memory."""
+    if name.startswith("lidar"):
+        pts = cloudgen.lidar_cloud(200000, seed=61)
+    elif name.startswith("room"):
+        pts = cloudgen.room_cloud(150000, seed=62)
+    else:
+        pts = cloudgen.uniform_cloud(120000, seed=63)
+    m = 6000
+    ref = oracle.fps(pts, m, 11, threads=0)
+    np.testing.assert_array_equal(gpu_fps(rf, pts, m, 11, **opts), ref)
