@@ -48,6 +48,8 @@ def parse():
                     choices=["room100k", "uniform4k", "lidar1m", "batch64", "serving"])
     ap.add_argument("--rate", type=float, default=200.0, help="serving: offered clouds per second")
     ap.add_argument("--requests", type=int, default=600, help="serving: timed requests")
+    ap.add_argument("--slots", type=int, default=32, help="serving: micro-batches in flight (one stream each)")
+    ap.add_argument("--max-batch", type=int, default=8, help="serving: clouds per micro-batch")
     ap.add_argument("--opts", default="", help="JSON dict of rfps_opts overrides")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -304,16 +306,17 @@ def run_batch64(args, rf, torch):
 def run_serving(args, rf):
     """Poisson request stream through the continuous-batching server."""
     from paper_2606_06255_gb300 import serve
-    opts = json.loads(args.opts) if args.opts else {"cluster": 4}
+    # throughput setting: one CTA of 512 threads per cloud (the most SM-efficient shape), many streams
+    opts = json.loads(args.opts) if args.opts else {"cluster": 1, "threads": 512}
     reqs = serve.poisson_workload(args.requests + 16, args.rate)
-    ex = serve.GpuExecutor(8, opts=opts)
-    srv = serve.Server(ex, mem_budget=48 << 30, max_inflight=8, max_batch=8)
+    ex = serve.GpuExecutor(args.slots, opts=opts)
+    srv = serve.Server(ex, mem_budget=48 << 30, max_inflight=args.slots, max_batch=args.max_batch)
     srv.run(reqs[:16])
     t0 = reqs[16].arrival
     rep = srv.run([serve.Request(r.rid, r.arrival - t0, r.points, r.m, r.start) for r in reqs[16:]])
     out = rep.summary()
     out.update({"metric": "p99 latency / clouds/s", "workload": "serving", "offered_rate": args.rate,
-                "requests": args.requests, "opts": opts, "slots": 8, "max_batch": 8,
+                "requests": args.requests, "opts": opts, "slots": args.slots, "max_batch": args.max_batch,
                 "sizes": "N log-uniform [20000, 1200000], M = N/8, half room / half LiDAR"})
     print(json.dumps(out), flush=True)
     return 0

@@ -232,10 +232,10 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description="Serve a Poisson stream of RadiusFPS requests on one GPU")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=200.0, help="offered arrivals per second")
-    ap.add_argument("--slots", type=int, default=8, help="micro-batches in flight (one stream each)")
+    ap.add_argument("--slots", type=int, default=32, help="micro-batches in flight (one stream each)")
     ap.add_argument("--max-batch", type=int, default=8)
     ap.add_argument("--mem-gb", type=float, default=32.0, help="device-memory budget for admitted work")
-    ap.add_argument("--opts", default='{"cluster": 4}')
+    ap.add_argument("--opts", default='{"cluster": 1, "threads": 512}')
     ap.add_argument("--warmup", type=int, default=16)
     args = ap.parse_args(argv)
     reqs = poisson_workload(args.requests + args.warmup, args.rate)
