@@ -308,7 +308,7 @@ def run_serving(args, rf):
     from paper_2606_06255_gb300 import serve
     # throughput setting: one CTA of 512 threads per cloud (the most SM-efficient shape), many streams
     opts = json.loads(args.opts) if args.opts else {"cluster": 1, "threads": 512}
-    reqs = serve.poisson_workload(args.requests + 16, args.rate)
+    reqs = serve.poisson_workload(args.requests + 16, args.rate, pinned=True)
     ex = serve.GpuExecutor(args.slots, opts=opts)
     srv = serve.Server(ex, mem_budget=48 << 30, max_inflight=args.slots, max_batch=args.max_batch)
     srv.run(reqs[:16])

@@ -30,7 +30,7 @@ import numpy as np
 class Request:
     rid: int
     arrival: float          # seconds after the start of the run
-    points: np.ndarray      # (N, 3) float32
+    points: np.ndarray      # (N, 3) float32 (or a pinned host tensor)
     m: int
     start: int = 0
 
@@ -55,6 +55,7 @@ class Report:
     rejected: list = field(default_factory=list)
     makespan: float = 0.0
     offered_rate: float = 0.0
+    window: tuple = (0.0, 0.0)       # first and last arrival
     max_inflight_batches: int = 0
     peak_mem: int = 0
 
@@ -62,7 +63,13 @@ class Report:
         lat = sorted(c.latency for c in self.completed)
         q = lambda p: lat[min(len(lat) - 1, int(round(p * (len(lat) - 1))))] if lat else None
         n = len(self.completed)
+        # completions per second over the middle half of the arrival window (steady state:
+        # equal to the offered rate when the server keeps up)
+        t0, t1 = self.window
+        a, b = t0 + 0.25 * (t1 - t0), t0 + 0.75 * (t1 - t0)
+        steady = sum(1 for c in self.completed if a <= c.finished <= b)
         return {
+            "steady_clouds_per_s": steady / (b - a) if b > a else None,
             "requests_completed": n,
             "requests_rejected": len(self.rejected),
             "offered_clouds_per_s": self.offered_rate,
@@ -94,6 +101,7 @@ class Server:
         if reqs:
             span = reqs[-1].arrival - reqs[0].arrival
             rep.offered_rate = (len(reqs) - 1) / span if span > 0 else float("inf")
+            rep.window = (reqs[0].arrival, reqs[-1].arrival)
         t0 = clock()
         i = 0
         queue = collections.deque()
@@ -150,17 +158,28 @@ class Server:
 
 
 class GpuExecutor:
-    """Runs micro-batches with the batched C ABI call, one CUDA stream per slot."""
+    """Runs micro-batches with the batched C ABI call, one CUDA stream per slot.
+
+    Per launch: each cloud's points are copied host -> device (pinned host
+    tensors are copied asynchronously; numpy arrays are staged through a
+    pinned buffer), the per-cloud offsets, sample counts and starts go up in
+    one pinned buffer, the batched call samples every cloud, and the indices
+    come back into a pinned buffer.  All of it is ordered on the slot's stream.
+    """
 
     def __init__(self, n_slots: int, opts=None, device=None):
+        import ctypes
+
         import torch
 
         from . import _lib
         self.torch = torch
         self.lib = _lib
+        self.ctypes = ctypes
         self.device = torch.device(device if device is not None else "cuda")
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(n_slots)]
         self.opts = opts
+        self._opts = _lib.Opts(**opts) if opts else None
 
     def mem_needed(self, batch) -> int:
         if not batch:
@@ -173,23 +192,44 @@ class GpuExecutor:
     def launch(self, batch, slot):
         torch = self.torch
         s = self.streams[slot]
-        sizes = [r.points.shape[0] for r in batch]
-        ms = [r.m for r in batch]
-        host = torch.empty((sum(sizes), 3), dtype=torch.float32, pin_memory=True)
-        hv = host.numpy()
-        o = 0
-        for r in batch:
-            hv[o:o + r.points.shape[0]] = r.points
-            o += r.points.shape[0]
+        b = len(batch)
+        sizes = [int(r.points.shape[0]) for r in batch]
+        ms = [int(r.m) for r in batch]
+        total, mtotal = sum(sizes), sum(ms)
+        meta = torch.empty(3 * b + 2, dtype=torch.int64, pin_memory=True)
+        mv = meta.numpy()
+        mv[0] = 0
+        mv[1:b + 1] = np.cumsum(sizes)
+        mv[b + 1] = 0
+        mv[b + 2:2 * b + 2] = np.cumsum(ms)
+        mv[2 * b + 2:] = [int(r.start) for r in batch]
+        staged = []
         with torch.cuda.stream(s):
-            pts = host.to(self.device, non_blocking=True)
-            out, ooff = self.lib.fps_batched(pts, sizes, ms, [r.start for r in batch], opts=self.opts, stream=s)
-            host_out = torch.empty(out.shape, dtype=torch.int64, pin_memory=True)
+            pts = torch.empty((total, 3), dtype=torch.float32, device=self.device)
+            o = 0
+            for r in batch:
+                src = r.points
+                if not isinstance(src, torch.Tensor):
+                    src = torch.from_numpy(np.ascontiguousarray(src, dtype=np.float32)).pin_memory()
+                    staged.append(src)
+                pts[o:o + src.shape[0]].copy_(src, non_blocking=True)
+                o += src.shape[0]
+            dmeta = meta.to(self.device, non_blocking=True)
+            ws = torch.empty(self.lib.batch_workspace_size(total, b, max(sizes), self.opts), dtype=torch.uint8,
+                             device=self.device)
+            out = torch.empty(mtotal, dtype=torch.int64, device=self.device)
+            base = dmeta.data_ptr()
+            self.lib._check(self.lib.lib().rfps_fps_batched(
+                pts.data_ptr(), total, base, b, base + 8 * (b + 1), base + 16 * (b + 1), max(sizes),
+                out.data_ptr(), self.ctypes.byref(self._opts) if self._opts is not None else None,
+                ws.data_ptr(), ws.numel(), s.cuda_stream), "rfps_fps_batched")
+            host_out = torch.empty(mtotal, dtype=torch.int64, pin_memory=True)
             host_out.copy_(out, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(s)
-        # keep the device buffers alive until the event completes
-        return {"event": ev, "host_out": host_out, "ooff": ooff, "keep": (host, pts, out)}
+        ooff = np.concatenate([[0], np.cumsum(ms)])
+        # keep every buffer alive until the event completes
+        return {"event": ev, "host_out": host_out, "ooff": ooff, "keep": (meta, dmeta, pts, ws, out, staged)}
 
     def done(self, handle) -> bool:
         return handle["event"].query()
@@ -200,12 +240,13 @@ class GpuExecutor:
 
 
 def poisson_workload(n_requests: int, rate: float, lo: int = 20000, hi: int = 1200000, ratio: float = 0.125,
-                     pool: int = 48, seed: int = 0):
+                     pool: int = 48, seed: int = 0, pinned: bool = False):
     """Poisson arrivals of room-like / LiDAR-like clouds with N log-uniform in [lo, hi] and M = N * ratio.
 
     A pool of distinct seeded clouds (drawn from the same size and kind
     distribution) is generated once and requests cycle through it, which keeps
-    host memory bounded for long runs.
+    host memory bounded for long runs.  pinned=True keeps the pool in pinned
+    host memory (requests then arrive in page-locked buffers).
     """
     import math
 
@@ -219,6 +260,9 @@ def poisson_workload(n_requests: int, rate: float, lo: int = 20000, hi: int = 12
             clouds.append(cloudgen.room_cloud(int(n), seed=seed * 1000 + k))
         else:
             clouds.append(cloudgen.lidar_cloud(int(n), seed=seed * 1000 + k, scan_seed=k // 2 % 4))
+    if pinned:
+        import torch
+        clouds = [torch.from_numpy(c).pin_memory() for c in clouds]
     t = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
     pick = rng.integers(0, pool, size=n_requests)
     return [Request(i, float(t[i]), clouds[pick[i]], max(1, int(clouds[pick[i]].shape[0] * ratio)), 0)
@@ -238,7 +282,7 @@ def main(argv=None):
     ap.add_argument("--opts", default='{"cluster": 1, "threads": 512}')
     ap.add_argument("--warmup", type=int, default=16)
     args = ap.parse_args(argv)
-    reqs = poisson_workload(args.requests + args.warmup, args.rate)
+    reqs = poisson_workload(args.requests + args.warmup, args.rate, pinned=True)
     ex = GpuExecutor(args.slots, opts=json.loads(args.opts))
     server = Server(ex, mem_budget=int(args.mem_gb * (1 << 30)), max_inflight=args.slots, max_batch=args.max_batch)
     server.run(reqs[:args.warmup])        # warm-up: kernel attributes, allocator pools
