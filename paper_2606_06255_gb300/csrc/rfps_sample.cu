@@ -134,6 +134,47 @@ __device__ __forceinline__ unsigned long long visit_points(float4* pts, const ui
     return lk;
 }
 
+// The same update for a record held in shared memory, one point per lane per
+// pass.  With 16 warps per CTA the other warps hide the shared-memory latency and
+// the unrolled, predicated slots above only lengthen the critical warp; with 8
+// warps the unrolled form is faster (both measured), so 512-thread CTAs use this.
+template <bool COUNTERS>
+__device__ __forceinline__ unsigned long long visit_points_smem(float4* pts, const uint32_t* orig, uint32_t off,
+                                                                uint32_t cnt, bool first, int skip, float sx,
+                                                                float sy, float sz, int lane, float& bx, float& by,
+                                                                float& bz, Cnt& k)
+{
+    unsigned long long lk = 0ull;
+#pragma unroll 1
+    for (uint32_t q = lane; q < cnt; q += 32) {
+        const float4 p = pts[off + q];
+        float d2 = first ? __int_as_float(0x7f800000) : p.w;
+        const float dx = __fsub_rn(p.x, sx);
+        const float dy = __fsub_rn(p.y, sy);
+        const float dz = __fsub_rn(p.z, sz);
+        const float xx = __fmul_rn(dx, dx), yy = __fmul_rn(dy, dy), zz = __fmul_rn(dz, dz);
+        bool write = first;
+        if (skip && skip_point(xx, yy, zz, d2)) {
+            if (COUNTERS) ++k.skip;
+        } else {
+            const float nd = __fadd_rn(__fadd_rn(xx, yy), zz);
+            if (nd < d2) {
+                d2 = nd;
+                write = true;
+                if (COUNTERS) ++k.upd;
+            }
+        }
+        if (write) pts[off + q].w = d2;
+        if (COUNTERS) ++k.visit;
+        const unsigned long long kk = make_key(d2, orig[off + q]);
+        if (kk > lk) {
+            lk = kk;
+            bx = p.x; by = p.y; bz = p.z;
+        }
+    }
+    return lk;
+}
+
 template <int NT>
 __device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t v, uint32_t* s_scr, uint32_t* total)
 {
@@ -409,20 +450,23 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             }
                         }
                     }
-                    const uint32_t nkeep = __popc(um);
-                    uint32_t incl = nkeep;
+                    if (!CLUSTER) {
+                        const uint32_t nkeep = __popc(um);
+                        uint32_t incl = nkeep;
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-                        if (lane >= o) incl += u;
-                    }
-                    const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
-                    if (wtot) {
-                        uint32_t base = 0;
-                        if (lane == 31) base = atomicAdd(&s_wlc[par], wtot);
-                        base = __shfl_sync(0xffffffffu, base, 31);
-                        uint32_t pos = base + incl - nkeep;
-                        for (uint32_t mm = um; mm; mm &= mm - 1) s_wl[pos++] = static_cast<uint32_t>(__ffs(mm) - 1) * NT + my;
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                            if (lane >= o) incl += u;
+                        }
+                        const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+                        if (wtot) {
+                            uint32_t base = 0;
+                            if (lane == 31) base = atomicAdd(&s_wlc[par], wtot);
+                            base = __shfl_sync(0xffffffffu, base, 31);
+                            uint32_t pos = base + incl - nkeep;
+                            for (uint32_t mm = um; mm; mm &= mm - 1)
+                                s_wl[pos++] = static_cast<uint32_t>(__ffs(mm) - 1) * NT + my;
+                        }
                     }
                     // ---- partial max over my records that are not revisited this iteration
                     const bool lrec_visited = lrec != 0xffffffffu && ((um >> (lrec / NT)) & 1u);
@@ -443,21 +487,41 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     dirty = um != 0;
                     pk = lkey;
                     prec = lrec;
-                    __syncthreads();
-                    if (CLUSTER && s_abort) break;   // uniform: read after the barrier
-                    if (t == 0) s_wlc[par ^ 1] = 0;
-                    // ---- one warp per unpruned record
-                    const uint32_t nwl = s_wlc[par];
-                    for (uint32_t i = w; i < nwl; i += NW) {
-                        const uint32_t l = s_wl[i];
+                    // ---- one warp per unpruned record.  Inside a cluster every warp visits the
+                    // records its own lanes hold (record l belongs to slot l mod NT, and consecutive
+                    // records, which are neighbours in Morton order, fall to different warps), so a
+                    // warp's iteration needs no CTA barrier: the cluster exchange is its only wait.
+                    // A single CTA shares the unpruned records out through a CTA worklist instead.
+                    uint32_t rem = um, nwl = 0;
+                    if (!CLUSTER) {
+                        __syncthreads();
+                        if (t == 0) s_wlc[par ^ 1] = 0;
+                        nwl = s_wlc[par];
+                    }
+                    for (uint32_t i = w;;) {
+                        uint32_t l;
+                        if (CLUSTER) {
+                            const uint32_t ball = __ballot_sync(0xffffffffu, rem != 0u);
+                            if (!ball) break;
+                            const int src = __ffs(ball) - 1;
+                            const uint32_t mm = __shfl_sync(0xffffffffu, rem, src);
+                            l = static_cast<uint32_t>(__ffs(mm) - 1) * NT + static_cast<uint32_t>(src * NW + w);
+                            if (lane == src) rem &= rem - 1u;
+                        } else {
+                            if (i >= nwl) break;
+                            l = s_wl[i];
+                            i += NW;
+                        }
                         const uint2 rg = v.rng[l];
                         float bx = 0.f, by = 0.f, bz = 0.f;
                         const bool in_smem = resident && (rg.x & kResident);
                         const unsigned long long lk =
-                            in_smem ? visit_points<PPL, COUNTERS>(s_pts, s_orig, rg.x & ~kResident, rg.y, first,
-                                                                  a.skip, sx, sy, sz, lane, bx, by, bz, cn)
-                                    : visit_points<PPL, COUNTERS>(a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx,
-                                                                  sy, sz, lane, bx, by, bz, cn);
+                            !in_smem ? visit_points<PPL, COUNTERS>(a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx,
+                                                                   sy, sz, lane, bx, by, bz, cn)
+                            : NT >= 512 ? visit_points_smem<COUNTERS>(s_pts, s_orig, rg.x & ~kResident, rg.y,
+                                                                      first, a.skip, sx, sy, sz, lane, bx, by, bz, cn)
+                                        : visit_points<PPL, COUNTERS>(s_pts, s_orig, rg.x & ~kResident, rg.y, first,
+                                                                      a.skip, sx, sy, sz, lane, bx, by, bz, cn);
                         unsigned long long rk;
                         const int wl = warp_argmax_lane(lk, &rk);
                         const float wx = __shfl_sync(0xffffffffu, bx, wl);
@@ -646,6 +710,9 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         atomicCAS(&a.hdr->status, 0u, kStatusTimeout);
                         s_abort = 1;
                     }
+                    // the fast path has no CTA barrier per iteration: each warp leaves on its own once
+                    // any warp of the CTA gave up (the others then time out in turn, each wait bounded)
+                    if (fast && __any_sync(0xffffffffu, *static_cast<volatile uint32_t*>(&s_abort) != 0u)) break;
                     unsigned long long kk = 0ull;
                     uint32_t ki = 0;
                     for (uint32_t q = lane; q < nslot; q += 32) {

@@ -57,6 +57,8 @@ OPT_GRID = [
     dict(cluster=4, threads=512, chunk=256, n_vox=24, skip=0),
     dict(cluster=2, threads=512, chunk=256, n_vox=24, prune=0, skip=0),
     dict(cluster=2, threads=512, chunk=256, n_vox=20, radius_mode=1),
+    dict(cluster=1, threads=512, chunk=64, n_vox=12, prune=0),
+    dict(cluster=16, threads=512, chunk=128, n_vox=24, skip=0),
     dict(n_vox=1),
     dict(n_vox=256, chunk=32),
 ]
