@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
     constexpr int NSLOT = CLUSTER ? kMaxCluster * NW : 1;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long s_wkey[2][NW];
-    __shared__ uint32_t s_wrec[2][NW];
+    __shared__ float4 s_wxyz[2][NW];
     __shared__ unsigned long long s_ckey[2][NSLOT];
     __shared__ float4 s_cxyz[2][NSLOT];
     __shared__ uint32_t s_scr[NW + 1];
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
             v.gbase = gbase;
             float4* s_pts = nullptr;
             uint32_t* s_orig = nullptr;
-            uint32_t* s_wl = nullptr;
+            uint32_t* s_soff = nullptr;
             bool resident = false;
             // hierarchical path (records in global memory, super-records in shared memory)
             float4* s_sct = nullptr;             // super centre, prune threshold
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                 v.best = v.ct + nloc;
                 v.key = reinterpret_cast<unsigned long long*>(v.best + nloc);
                 v.rng = reinterpret_cast<uint2*>(v.key + nloc);
-                s_wl = reinterpret_cast<uint32_t*>(v.rng + nloc);
+                s_soff = reinterpret_cast<uint32_t*>(v.rng + nloc);
                 const size_t poff = (static_cast<size_t>(nloc) * 52 + 15) & ~static_cast<size_t>(15);
                 s_pts = reinterpret_cast<float4*>(smem + poff);
                 const uint32_t P = static_cast<uint32_t>((a.smem_bytes - poff) / 20);
@@ -318,13 +318,13 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     uint32_t off = block_exclusive_sum<NT>(sum, s_scr, &total);
                     for (uint32_t l = l0; l < l1; ++l) {
                         const uint32_t cnt = v.rng[l].y;
-                        s_wl[l] = (off + cnt <= P) ? off : 0xffffffffu;   // staging: worklist not in use yet
+                        s_soff[l] = (off + cnt <= P) ? off : 0xffffffffu;   // shared-memory offset, or not resident
                         off += cnt;
                     }
                     __syncthreads();
                     for (uint32_t l = w; l < nloc; l += NW) {
                         const uint2 rg = v.rng[l];
-                        const uint32_t so = s_wl[l];
+                        const uint32_t so = s_soff[l];
                         if (so == 0xffffffffu) continue;
                         for (uint32_t q = lane; q < rg.y; q += 32) {
                             s_pts[so + q] = a.pts4[rg.x + q];
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     }
                     __syncthreads();
                     for (uint32_t l = t; l < nloc; l += NT)
-                        if (s_wl[l] != 0xffffffffu) v.rng[l].x = kResident | s_wl[l];
+                        if (s_soff[l] != 0xffffffffu) v.rng[l].x = kResident | s_soff[l];
                     resident = true;
                 }
             } else {
@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
             float sy = resume ? c.last[1] : a.pts[3 * g0 + 1];
             float sz = resume ? c.last[2] : a.pts[3 * g0 + 2];
             if (t == 0) {
-                s_wlc[0] = 0;   // every CTA's own worklist counters
+                s_wlc[0] = 0;   // every CTA's own list counters (hierarchical path)
                 s_wlc[1] = 0;
                 s_rlc[0] = 0;
                 s_rlc[1] = 0;
@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                 unsigned long long pk;   // this lane's partial max (key, record) for the selection
                 uint32_t prec;
                 if (fast) {
-                    // ---- prune test of my records; unpruned ones go to the CTA worklist
+                    // ---- prune test of my records (bit b of um: record b * NT + my is kept)
                     const int nb = static_cast<int>((nloc + NT - 1) / NT);
                     uint32_t um = 0;
                     for (int b = 0; b < nb; ++b) {
@@ -448,24 +448,6 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                                 ++cn.tests;
                                 cn.pruned += keep ? 0 : 1;
                             }
-                        }
-                    }
-                    if (!CLUSTER) {
-                        const uint32_t nkeep = __popc(um);
-                        uint32_t incl = nkeep;
-#pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-                            if (lane >= o) incl += u;
-                        }
-                        const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
-                        if (wtot) {
-                            uint32_t base = 0;
-                            if (lane == 31) base = atomicAdd(&s_wlc[par], wtot);
-                            base = __shfl_sync(0xffffffffu, base, 31);
-                            uint32_t pos = base + incl - nkeep;
-                            for (uint32_t mm = um; mm; mm &= mm - 1)
-                                s_wl[pos++] = static_cast<uint32_t>(__ffs(mm) - 1) * NT + my;
                         }
                     }
                     // ---- partial max over my records that are not revisited this iteration
@@ -487,31 +469,19 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     dirty = um != 0;
                     pk = lkey;
                     prec = lrec;
-                    // ---- one warp per unpruned record.  Inside a cluster every warp visits the
-                    // records its own lanes hold (record l belongs to slot l mod NT, and consecutive
-                    // records, which are neighbours in Morton order, fall to different warps), so a
-                    // warp's iteration needs no CTA barrier: the cluster exchange is its only wait.
-                    // A single CTA shares the unpruned records out through a CTA worklist instead.
-                    uint32_t rem = um, nwl = 0;
-                    if (!CLUSTER) {
-                        __syncthreads();
-                        if (t == 0) s_wlc[par ^ 1] = 0;
-                        nwl = s_wlc[par];
-                    }
-                    for (uint32_t i = w;;) {
-                        uint32_t l;
-                        if (CLUSTER) {
-                            const uint32_t ball = __ballot_sync(0xffffffffu, rem != 0u);
-                            if (!ball) break;
-                            const int src = __ffs(ball) - 1;
-                            const uint32_t mm = __shfl_sync(0xffffffffu, rem, src);
-                            l = static_cast<uint32_t>(__ffs(mm) - 1) * NT + static_cast<uint32_t>(src * NW + w);
-                            if (lane == src) rem &= rem - 1u;
-                        } else {
-                            if (i >= nwl) break;
-                            l = s_wl[i];
-                            i += NW;
-                        }
+                    // ---- one warp per unpruned record: every warp visits the records its own lanes
+                    // hold (record l belongs to slot l mod NT, and consecutive records, which are
+                    // neighbours in Morton order, fall to different warps).  Record state is then
+                    // touched by one warp only, so the record work needs no CTA barrier: the selection
+                    // below is the iteration's only wait.
+                    uint32_t rem = um;
+                    for (;;) {
+                        const uint32_t ball = __ballot_sync(0xffffffffu, rem != 0u);
+                        if (!ball) break;
+                        const int src = __ffs(ball) - 1;
+                        const uint32_t mm = __shfl_sync(0xffffffffu, rem, src);
+                        const uint32_t l = static_cast<uint32_t>(__ffs(mm) - 1) * NT + static_cast<uint32_t>(src * NW + w);
+                        if (lane == src) rem &= rem - 1u;
                         const uint2 rg = v.rng[l];
                         float bx = 0.f, by = 0.f, bz = 0.f;
                         const bool in_smem = resident && (rg.x & kResident);
@@ -680,16 +650,16 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                 float4 cxyz = make_float4(0.f, 0.f, 0.f, 0.f);
                 unsigned long long gbest;
                 if (!CLUSTER) {
+                    // each warp publishes its candidate's key and coordinates (the record's owner
+                    // may rewrite its best point in the next iteration, before a slower warp reads it)
                     if (lane == 0) {
                         s_wkey[par][w] = wk;
-                        s_wrec[par][w] = wr;
+                        s_wxyz[par][w] = wk != 0ull ? (fast ? v.best[wr] : s_sxyz[wr]) : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                     __syncthreads();
                     const unsigned long long ck = lane < NW ? s_wkey[par][lane] : 0ull;
-                    uint32_t cr = lane < NW ? s_wrec[par][lane] : 0xffffffffu;
                     const int cl = warp_argmax_lane(ck, &gbest);
-                    cr = __shfl_sync(0xffffffffu, cr, cl);
-                    if (gbest != 0ull) cxyz = fast ? v.best[cr] : s_sxyz[cr];
+                    cxyz = s_wxyz[par][cl];
                 } else {
                     // Every warp pushes its best (key, xyz) by st.async into slot [rank][warp] of every
                     // CTA; each CTA's barrier for this round expects C * NW * 24 bytes.  (Reducing in the
