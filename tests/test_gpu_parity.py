@@ -295,3 +295,31 @@ def test_hierarchical_path_many_records(rf, name, opts):
     m = 6000
     ref = oracle.fps(pts, m, 11, threads=0)
     np.testing.assert_array_equal(gpu_fps(rf, pts, m, 11, **opts), ref)
+
+
+def _lattice(nx, ny, nz):
+    g = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    return np.stack([a.ravel() for a in g], 1).astype(np.float32)
+
+
+@pytest.mark.parametrize("opts", [
+    dict(cluster=2, threads=256), dict(cluster=4, threads=512), dict(cluster=8, threads=256),
+    dict(cluster=16, threads=256), dict(cluster=16, threads=512),
+], ids=lambda o: "c%d_t%d" % (o["cluster"], o["threads"]))
+def test_exact_ties_across_cluster_exchange(rf, opts):
+    """Equal squared distances in different warps and CTAs: the smallest point index must win (Sec. 3.1)."""
+    grid = _lattice(16, 16, 16)
+    np.testing.assert_array_equal(gpu_fps(rf, grid, 2000, 7, **opts), oracle.fps(grid, 2000, 7))
+    base = cloudgen.uniform_cloud(3000, seed=71)
+    dup = base[np.random.default_rng(72).permutation(np.repeat(np.arange(3000), 3))]
+    # past 3000 samples every remaining candidate is at distance 0: each round is a tie
+    np.testing.assert_array_equal(gpu_fps(rf, dup, 4000, 0, **opts), oracle.fps(dup, 4000, 0))
+    same = np.tile(np.array([[0.5, 0.25, -3.0]], np.float32), (1000, 1))
+    np.testing.assert_array_equal(gpu_fps(rf, same, 50, 999, **opts), oracle.fps(same, 50, 999))
+
+
+def test_exact_ties_hierarchical_cluster(rf):
+    """Ties on the hierarchical path (records in global memory) inside a 2-CTA cluster."""
+    grid = _lattice(64, 64, 48)
+    ref = oracle.fps(grid, 3000, 5, threads=0)
+    np.testing.assert_array_equal(gpu_fps(rf, grid, 3000, 5, cluster=2, n_vox=64, chunk=32), ref)
