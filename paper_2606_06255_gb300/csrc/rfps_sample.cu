@@ -233,6 +233,17 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
     }
     if (CLUSTER) cluster_sync();       // barriers initialised, every CTA running before any DSMEM store
     else __syncthreads();
+    // this lane's destination (CTA `lane` of the cluster) for both exchange buffers: slot
+    // [rank][warp] of the keys and coordinates, and that CTA's barrier
+    uint32_t rkey0 = 0, rkey1 = 0, rxyz0 = 0, rxyz1 = 0, rbar0 = 0, rbar1 = 0;
+    if (CLUSTER && lane < static_cast<int>(C)) {
+        rkey0 = map_shared(&s_ckey[0][rank * NW + w], lane);
+        rkey1 = map_shared(&s_ckey[1][rank * NW + w], lane);
+        rxyz0 = map_shared(&s_cxyz[0][rank * NW + w], lane);
+        rxyz1 = map_shared(&s_cxyz[1][rank * NW + w], lane);
+        rbar0 = map_shared(&s_mbar[0], lane);
+        rbar1 = map_shared(&s_mbar[1], lane);
+    }
     uint32_t it = 0;                   // exchange rounds so far (same count in every CTA of the cluster)
     const float nan = __int_as_float(0x7fc00000);
     const uint32_t my = static_cast<uint32_t>(lane * NW + w);   // my slot inside each batch of NT records
@@ -672,21 +683,23 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     float4 wxyz = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (wk != 0ull && lane < static_cast<int>(C)) wxyz = fast ? v.best[wr] : s_sxyz[wr];
                     if (lane < static_cast<int>(C)) {
-                        const uint32_t rb = map_shared(&s_mbar[buf], lane);
-                        st_async_u64(map_shared(&s_ckey[buf][rank * NW + w], lane), wk, rb);
-                        st_async_f32x4(map_shared(&s_cxyz[buf][rank * NW + w], lane), wxyz, rb);
+                        const uint32_t rb = buf ? rbar1 : rbar0;
+                        st_async_u64(buf ? rkey1 : rkey0, wk, rb);
+                        st_async_f32x4(buf ? rxyz1 : rxyz0, wxyz, rb);
                     }
-                    if (!mbar_wait_bounded(&s_mbar[buf], ph, kSpinLimit)) {
-                        atomicCAS(&a.hdr->status, 0u, kStatusTimeout);
+                    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&s_mbar[buf], ph, kSpinLimit))) {
+                        if (lane == 0) atomicCAS(&a.hdr->status, 0u, kStatusTimeout);
                         s_abort = 1;
+                        // the fast path has no CTA barrier per iteration: this warp leaves on its own,
+                        // and the other warps of the cluster time out in turn (each wait bounded)
+                        if (fast) break;
                     }
-                    // the fast path has no CTA barrier per iteration: each warp leaves on its own once
-                    // any warp of the CTA gave up (the others then time out in turn, each wait bounded)
-                    if (fast && __any_sync(0xffffffffu, *static_cast<volatile uint32_t*>(&s_abort) != 0u)) break;
                     unsigned long long kk = 0ull;
                     uint32_t ki = 0;
-                    for (uint32_t q = lane; q < nslot; q += 32) {
-                        const unsigned long long x = s_ckey[buf][q];
+#pragma unroll
+                    for (int u = 0; u < NSLOT / 32; ++u) {   // every slot, unrolled; unused ones read as 0
+                        const uint32_t q = static_cast<uint32_t>(u * 32 + lane);
+                        const unsigned long long x = q < nslot ? s_ckey[buf][q] : 0ull;
                         if (x > kk) {
                             kk = x;
                             ki = q;
