@@ -204,6 +204,11 @@ __device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t v, uint32_t* s_
     return before + inc - v;
 }
 
+template <int V>
+struct IntC {
+    static constexpr int value = V;
+};
+
 template <int NT, bool CLUSTER, bool COUNTERS>
 __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
 {
@@ -441,281 +446,316 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
             bool dirty = true;
             __syncthreads();
 
-            for (int64_t j = 1; j < c.m; ++j) {
-                const bool first = (j == 1) && !resume;   // the initial update of Sec. 3.3
-                const int par = static_cast<int>(j & 1);
-                unsigned long long pk;   // this lane's partial max (key, record) for the selection
-                uint32_t prec;
-                if (fast) {
-                    // ---- prune test of my records (bit b of um: record b * NT + my is kept)
-                    const int nb = static_cast<int>((nloc + NT - 1) / NT);
-                    uint32_t um = 0;
-                    for (int b = 0; b < nb; ++b) {
-                        const uint32_t l = static_cast<uint32_t>(b) * NT + my;
-                        if (l < nloc) {
-                            const bool keep = first || !a.prune || !prune_by_threshold(v.ct[l], sx, sy, sz);
-                            um |= keep ? (1u << b) : 0u;
+            // The iteration loop, compiled once per path so that each is scheduled on its own:
+            // MODE 0 hierarchical; 1 and 2 fast with this lane's one or two records' centres and
+            // thresholds held in registers (nloc <= NT, <= 2 NT; 256-thread CTAs, whose register
+            // budget has room for it); 3 fast with any number per lane.
+            const int nb = static_cast<int>((nloc + NT - 1) / NT);
+            auto iterate = [&](auto mode) {
+                constexpr int MODE = decltype(mode)::value;
+                constexpr bool FAST = MODE != 0;
+                constexpr int NREG = MODE == 1 || MODE == 2 ? MODE : 0;
+                float4 ct0 = make_float4(0.f, 0.f, 0.f, 0.f), ct1 = ct0;
+                if constexpr (NREG > 0) {
+                    if (my < nloc) ct0 = v.ct[my];
+                    if (NREG == 2 && my + NT < nloc) ct1 = v.ct[my + NT];
+                }
+                for (int64_t j = 1; j < c.m; ++j) {
+                    const bool first = (j == 1) && !resume;   // the initial update of Sec. 3.3
+                    const int par = static_cast<int>(j & 1);
+                    unsigned long long pk;   // this lane's partial max (key, record) for the selection
+                    uint32_t prec;
+                    uint32_t vis = 0;        // my records visited now (bit b: record b * NT + my)
+                    if constexpr (FAST) {
+                        // ---- prune test of my records (bit b of um: record b * NT + my is kept)
+                        uint32_t um = 0;
+                        if constexpr (NREG > 0) {
+                            const bool h0 = my < nloc, h1 = NREG == 2 && my + NT < nloc;
+                            const bool k0 = h0 && (first || !a.prune || !prune_by_threshold(ct0, sx, sy, sz));
+                            const bool k1 = h1 && (first || !a.prune || !prune_by_threshold(ct1, sx, sy, sz));
+                            um = (k0 ? 1u : 0u) | (k1 ? 2u : 0u);
                             if (COUNTERS && !first) {
-                                ++cn.tests;
-                                cn.pruned += keep ? 0 : 1;
+                                cn.tests += (h0 ? 1 : 0) + (h1 ? 1 : 0);
+                                cn.pruned += (h0 && !k0 ? 1 : 0) + (h1 && !k1 ? 1 : 0);
                             }
-                        }
-                    }
-                    // ---- partial max over my records that are not revisited this iteration
-                    const bool lrec_visited = lrec != 0xffffffffu && ((um >> (lrec / NT)) & 1u);
-                    if (dirty || lrec_visited) {
-                        lkey = 0ull;
-                        lrec = 0xffffffffu;
-                        for (int b = 0; b < nb; ++b) {
-                            const uint32_t l = static_cast<uint32_t>(b) * NT + my;
-                            if (l < nloc && !((um >> b) & 1u)) {
-                                const unsigned long long kk = v.key[l];
-                                if (kk > lkey) {
-                                    lkey = kk;
-                                    lrec = l;
+                        } else {
+                            for (int b = 0; b < nb; ++b) {
+                                const uint32_t l = static_cast<uint32_t>(b) * NT + my;
+                                if (l < nloc) {
+                                    const bool keep = first || !a.prune || !prune_by_threshold(v.ct[l], sx, sy, sz);
+                                    um |= keep ? (1u << b) : 0u;
+                                    if (COUNTERS && !first) {
+                                        ++cn.tests;
+                                        cn.pruned += keep ? 0 : 1;
+                                    }
                                 }
                             }
                         }
-                    }
-                    dirty = um != 0;
-                    pk = lkey;
-                    prec = lrec;
-                    // ---- one warp per unpruned record: every warp visits the records its own lanes
-                    // hold (record l belongs to slot l mod NT, and consecutive records, which are
-                    // neighbours in Morton order, fall to different warps).  Record state is then
-                    // touched by one warp only, so the record work needs no CTA barrier: the selection
-                    // below is the iteration's only wait.
-                    uint32_t rem = um;
-                    for (;;) {
-                        const uint32_t ball = __ballot_sync(0xffffffffu, rem != 0u);
-                        if (!ball) break;
-                        const int src = __ffs(ball) - 1;
-                        const uint32_t mm = __shfl_sync(0xffffffffu, rem, src);
-                        const uint32_t l = static_cast<uint32_t>(__ffs(mm) - 1) * NT + static_cast<uint32_t>(src * NW + w);
-                        if (lane == src) rem &= rem - 1u;
-                        const uint2 rg = v.rng[l];
-                        float bx = 0.f, by = 0.f, bz = 0.f;
-                        const bool in_smem = resident && (rg.x & kResident);
-                        const unsigned long long lk =
-                            !in_smem ? visit_points<PPL, COUNTERS>(a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx,
-                                                                   sy, sz, lane, bx, by, bz, cn)
-                            : NT >= 512 ? visit_points_smem<COUNTERS>(s_pts, s_orig, rg.x & ~kResident, rg.y,
-                                                                      first, a.skip, sx, sy, sz, lane, bx, by, bz, cn)
-                                        : visit_points<PPL, COUNTERS>(s_pts, s_orig, rg.x & ~kResident, rg.y, first,
-                                                                      a.skip, sx, sy, sz, lane, bx, by, bz, cn);
-                        unsigned long long rk;
-                        const int wl = warp_argmax_lane(lk, &rk);
-                        const float wx = __shfl_sync(0xffffffffu, bx, wl);
-                        const float wy = __shfl_sync(0xffffffffu, by, wl);
-                        const float wz = __shfl_sync(0xffffffffu, bz, wl);
-                        if (lane == 0) {
-                            const float r = v.best[l].w;
-                            v.key[l] = rk;
-                            v.best[l] = make_float4(wx, wy, wz, r);
-                            v.ct[l].w = prune_threshold(r, rk);
-                            if (rk > pk) {
-                                pk = rk;
-                                prec = l;
+                        // ---- partial max over my records that are not revisited this iteration
+                        const bool lrec_visited = lrec != 0xffffffffu && ((um >> (lrec / NT)) & 1u);
+                        if (dirty || lrec_visited) {
+                            lkey = 0ull;
+                            lrec = 0xffffffffu;
+                            for (int b = 0; b < (NREG > 0 ? NREG : nb); ++b) {
+                                const uint32_t l = static_cast<uint32_t>(b) * NT + my;
+                                if (l < nloc && !((um >> b) & 1u)) {
+                                    const unsigned long long kk = v.key[l];
+                                    if (kk > lkey) {
+                                        lkey = kk;
+                                        lrec = l;
+                                    }
+                                }
                             }
                         }
-                    }
-                } else {
-                    // one warp updates record l (global memory) and refreshes its key, best point
-                    // and prune threshold
-                    auto visit_global = [&](uint32_t l) {
-                        const uint32_t k = v.g(l);
-                        const uint2 rg = a.rec_rng[k];
-                        float bx = 0.f, by = 0.f, bz = 0.f;
-                        const unsigned long long lk = visit_points<PPL, COUNTERS>(
-                            a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx, sy, sz, lane, bx, by, bz, cn);
-                        unsigned long long rk;
-                        const int wl = warp_argmax_lane(lk, &rk);
-                        const float wx = __shfl_sync(0xffffffffu, bx, wl);
-                        const float wy = __shfl_sync(0xffffffffu, by, wl);
-                        const float wz = __shfl_sync(0xffffffffu, bz, wl);
-                        if (lane == 0) {
-                            const float r = a.rec_best[k].w;
-                            a.rec_key[k] = rk;
-                            a.rec_best[k] = make_float4(wx, wy, wz, r);
-                            a.rec_thr[k] = prune_threshold(r, rk);
-                        }
-                    };
-                    // ---- A1: prune test of my super-records; unpruned ones to the super list
-                    for (uint32_t g0s = 0; g0s < G; g0s += 32u * NT) {
-                        uint32_t su = 0;
-                        for (int b = 0; b < 32; ++b) {
-                            const uint32_t g = g0s + static_cast<uint32_t>(b) * NT + my;
-                            if (g >= G) break;
-                            const bool keep = first || !a.prune || !prune_by_threshold(s_sct[g], sx, sy, sz);
-                            su |= keep ? (1u << b) : 0u;
-                            if (COUNTERS && !first) {
-                                ++cn.tests;
-                                cn.pruned += keep ? 0 : 1;
+                        dirty = um != 0;
+                        vis = um;
+                        pk = lkey;
+                        prec = lrec;
+                        // ---- one warp per unpruned record: every warp visits the records its own lanes
+                        // hold (record l belongs to slot l mod NT, and consecutive records, which are
+                        // neighbours in Morton order, fall to different warps).  Record state is then
+                        // touched by one warp only, so the record work needs no CTA barrier: the selection
+                        // below is the iteration's only wait.
+                        uint32_t rem = um;
+                        for (;;) {
+                            const uint32_t ball = __ballot_sync(0xffffffffu, rem != 0u);
+                            if (!ball) break;
+                            const int src = __ffs(ball) - 1;
+                            const uint32_t mm = __shfl_sync(0xffffffffu, rem, src);
+                            const uint32_t l = static_cast<uint32_t>(__ffs(mm) - 1) * NT + static_cast<uint32_t>(src * NW + w);
+                            if (lane == src) rem &= rem - 1u;
+                            const uint2 rg = v.rng[l];
+                            float bx = 0.f, by = 0.f, bz = 0.f;
+                            const bool in_smem = resident && (rg.x & kResident);
+                            const unsigned long long lk =
+                                !in_smem ? visit_points<PPL, COUNTERS>(a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx,
+                                                                       sy, sz, lane, bx, by, bz, cn)
+                                : NT >= 512 ? visit_points_smem<COUNTERS>(s_pts, s_orig, rg.x & ~kResident, rg.y,
+                                                                          first, a.skip, sx, sy, sz, lane, bx, by, bz, cn)
+                                            : visit_points<PPL, COUNTERS>(s_pts, s_orig, rg.x & ~kResident, rg.y, first,
+                                                                          a.skip, sx, sy, sz, lane, bx, by, bz, cn);
+                            unsigned long long rk;
+                            const int wl = warp_argmax_lane(lk, &rk);
+                            const float wx = __shfl_sync(0xffffffffu, bx, wl);
+                            const float wy = __shfl_sync(0xffffffffu, by, wl);
+                            const float wz = __shfl_sync(0xffffffffu, bz, wl);
+                            if (lane == 0) {
+                                const float r = v.best[l].w;
+                                v.key[l] = rk;
+                                v.best[l] = make_float4(wx, wy, wz, r);
+                                v.ct[l].w = prune_threshold(r, rk);
+                                if (rk > pk) {
+                                    pk = rk;
+                                    prec = l;
+                                }
                             }
                         }
-                        const uint32_t nkeep = __popc(su);
-                        uint32_t incl = nkeep;
-#pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-                            if (lane >= o) incl += u;
+                    } else {
+                        // one warp updates record l (global memory) and refreshes its key, best point
+                        // and prune threshold
+                        auto visit_global = [&](uint32_t l) {
+                            const uint32_t k = v.g(l);
+                            const uint2 rg = a.rec_rng[k];
+                            float bx = 0.f, by = 0.f, bz = 0.f;
+                            const unsigned long long lk = visit_points<PPL, COUNTERS>(
+                                a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx, sy, sz, lane, bx, by, bz, cn);
+                            unsigned long long rk;
+                            const int wl = warp_argmax_lane(lk, &rk);
+                            const float wx = __shfl_sync(0xffffffffu, bx, wl);
+                            const float wy = __shfl_sync(0xffffffffu, by, wl);
+                            const float wz = __shfl_sync(0xffffffffu, bz, wl);
+                            if (lane == 0) {
+                                const float r = a.rec_best[k].w;
+                                a.rec_key[k] = rk;
+                                a.rec_best[k] = make_float4(wx, wy, wz, r);
+                                a.rec_thr[k] = prune_threshold(r, rk);
+                            }
+                        };
+                        // ---- A1: prune test of my super-records; unpruned ones to the super list
+                        for (uint32_t g0s = 0; g0s < G; g0s += 32u * NT) {
+                            uint32_t su = 0;
+                            for (int b = 0; b < 32; ++b) {
+                                const uint32_t g = g0s + static_cast<uint32_t>(b) * NT + my;
+                                if (g >= G) break;
+                                const bool keep = first || !a.prune || !prune_by_threshold(s_sct[g], sx, sy, sz);
+                                su |= keep ? (1u << b) : 0u;
+                                if (COUNTERS && !first) {
+                                    ++cn.tests;
+                                    cn.pruned += keep ? 0 : 1;
+                                }
+                            }
+                            const uint32_t nkeep = __popc(su);
+                            uint32_t incl = nkeep;
+    #pragma unroll
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                                if (lane >= o) incl += u;
+                            }
+                            const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+                            if (wtot) {
+                                uint32_t base = 0;
+                                if (lane == 31) base = atomicAdd(&s_wlc[par], wtot);
+                                base = __shfl_sync(0xffffffffu, base, 31);
+                                uint32_t pos = base + incl - nkeep;
+                                for (uint32_t mm = su; mm; mm &= mm - 1)
+                                    s_slist[pos++] = g0s + static_cast<uint32_t>(__ffs(mm) - 1) * NT + my;
+                            }
                         }
-                        const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
-                        if (wtot) {
+                        __syncthreads();
+                        if (CLUSTER && s_abort) break;   // uniform: read after the barrier
+                        if (t == 0) {
+                            s_wlc[par ^ 1] = 0;
+                            s_rlc[par ^ 1] = 0;
+                            s_rlcut[par ^ 1] = W;
+                        }
+                        const uint32_t nsl = s_wlc[par];
+                        // ---- A2: records of the unpruned super-records (one per lane); unpruned ones
+                        // go to the record list, or are visited in place when the list is full
+                        for (uint32_t i = w; i < nsl; i += NW) {
+                            const uint32_t g = s_slist[i];
+                            const uint32_t l = g * 32 + lane;
+                            bool keep = false;
+                            if (l < nloc) {
+                                if (first || !a.prune) {
+                                    keep = true;
+                                } else {
+                                    const uint32_t k = v.g(l);
+                                    const float4 sp = a.rec_sph[k];
+                                    keep = !prune_by_threshold(make_float4(sp.x, sp.y, sp.z, a.rec_thr[k]), sx, sy, sz);
+                                }
+                                if (COUNTERS && !first) {
+                                    ++cn.tests;
+                                    cn.pruned += keep ? 0 : 1;
+                                }
+                            }
+                            uint32_t mask = __ballot_sync(0xffffffffu, keep);
+                            if (!mask) continue;
                             uint32_t base = 0;
-                            if (lane == 31) base = atomicAdd(&s_wlc[par], wtot);
-                            base = __shfl_sync(0xffffffffu, base, 31);
-                            uint32_t pos = base + incl - nkeep;
-                            for (uint32_t mm = su; mm; mm &= mm - 1)
-                                s_slist[pos++] = g0s + static_cast<uint32_t>(__ffs(mm) - 1) * NT + my;
-                        }
-                    }
-                    __syncthreads();
-                    if (CLUSTER && s_abort) break;   // uniform: read after the barrier
-                    if (t == 0) {
-                        s_wlc[par ^ 1] = 0;
-                        s_rlc[par ^ 1] = 0;
-                        s_rlcut[par ^ 1] = W;
-                    }
-                    const uint32_t nsl = s_wlc[par];
-                    // ---- A2: records of the unpruned super-records (one per lane); unpruned ones
-                    // go to the record list, or are visited in place when the list is full
-                    for (uint32_t i = w; i < nsl; i += NW) {
-                        const uint32_t g = s_slist[i];
-                        const uint32_t l = g * 32 + lane;
-                        bool keep = false;
-                        if (l < nloc) {
-                            if (first || !a.prune) {
-                                keep = true;
+                            if (lane == 0) base = atomicAdd(&s_rlc[par], static_cast<uint32_t>(__popc(mask)));
+                            base = __shfl_sync(0xffffffffu, base, 0);
+                            if (base + __popc(mask) <= W) {
+                                if (keep) s_rlist[base + __popc(mask & ((1u << lane) - 1u))] = l;
                             } else {
-                                const uint32_t k = v.g(l);
-                                const float4 sp = a.rec_sph[k];
-                                keep = !prune_by_threshold(make_float4(sp.x, sp.y, sp.z, a.rec_thr[k]), sx, sy, sz);
-                            }
-                            if (COUNTERS && !first) {
-                                ++cn.tests;
-                                cn.pruned += keep ? 0 : 1;
+                                // list full: later appends fail too, so the list holds [0, first failed base)
+                                if (lane == 0) atomicMin(&s_rlcut[par], base);
+                                while (mask) {
+                                    const int src = __ffs(mask) - 1;
+                                    mask &= mask - 1;
+                                    visit_global(g * 32 + static_cast<uint32_t>(src));
+                                }
                             }
                         }
-                        uint32_t mask = __ballot_sync(0xffffffffu, keep);
-                        if (!mask) continue;
-                        uint32_t base = 0;
-                        if (lane == 0) base = atomicAdd(&s_rlc[par], static_cast<uint32_t>(__popc(mask)));
-                        base = __shfl_sync(0xffffffffu, base, 0);
-                        if (base + __popc(mask) <= W) {
-                            if (keep) s_rlist[base + __popc(mask & ((1u << lane) - 1u))] = l;
-                        } else {
-                            // list full: later appends fail too, so the list holds [0, first failed base)
-                            if (lane == 0) atomicMin(&s_rlcut[par], base);
-                            while (mask) {
-                                const int src = __ffs(mask) - 1;
-                                mask &= mask - 1;
-                                visit_global(g * 32 + static_cast<uint32_t>(src));
+                        __syncthreads();
+                        // ---- B: one warp per listed record
+                        const uint32_t nrl = min(min(s_rlc[par], s_rlcut[par]), W);
+                        for (uint32_t i = w; i < nrl; i += NW) visit_global(s_rlist[i]);
+                        __syncthreads();
+                        // ---- C: refresh the unpruned super-records from their records
+                        for (uint32_t i = w; i < nsl; i += NW) {
+                            const uint32_t g = s_slist[i];
+                            const uint32_t l = g * 32 + lane;
+                            unsigned long long kk = 0ull;
+                            float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (l < nloc) {
+                                kk = a.rec_key[v.g(l)];
+                                b4 = a.rec_best[v.g(l)];
+                            }
+                            unsigned long long gk;
+                            const int gl = warp_argmax_lane(kk, &gk);
+                            const float bx = __shfl_sync(0xffffffffu, b4.x, gl);
+                            const float by = __shfl_sync(0xffffffffu, b4.y, gl);
+                            const float bz = __shfl_sync(0xffffffffu, b4.z, gl);
+                            if (lane == 0) {
+                                const float srad = s_sxyz[g].w;
+                                s_skey[g] = gk;
+                                s_sxyz[g] = make_float4(bx, by, bz, srad);
+                                s_sct[g].w = prune_threshold(srad, gk);
+                            }
+                        }
+                        __syncthreads();
+                        // ---- D: my super-records' max
+                        pk = 0ull;
+                        prec = 0xffffffffu;
+                        for (uint32_t g = my; g < G; g += NT) {
+                            const unsigned long long kk = s_skey[g];
+                            if (kk > pk) {
+                                pk = kk;
+                                prec = g;
                             }
                         }
                     }
-                    __syncthreads();
-                    // ---- B: one warp per listed record
-                    const uint32_t nrl = min(min(s_rlc[par], s_rlcut[par]), W);
-                    for (uint32_t i = w; i < nrl; i += NW) visit_global(s_rlist[i]);
-                    __syncthreads();
-                    // ---- C: refresh the unpruned super-records from their records
-                    for (uint32_t i = w; i < nsl; i += NW) {
-                        const uint32_t g = s_slist[i];
-                        const uint32_t l = g * 32 + lane;
-                        unsigned long long kk = 0ull;
-                        float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (l < nloc) {
-                            kk = a.rec_key[v.g(l)];
-                            b4 = a.rec_best[v.g(l)];
-                        }
-                        unsigned long long gk;
-                        const int gl = warp_argmax_lane(kk, &gk);
-                        const float bx = __shfl_sync(0xffffffffu, b4.x, gl);
-                        const float by = __shfl_sync(0xffffffffu, b4.y, gl);
-                        const float bz = __shfl_sync(0xffffffffu, b4.z, gl);
+                    // ---- selection: warp -> CTA -> cluster
+                    __syncwarp();
+                    if constexpr (NREG > 0) {   // thresholds rewritten by this iteration's visits
+                        if (vis & 1u) ct0.w = v.ct[my].w;
+                        if (NREG == 2 && (vis & 2u)) ct1.w = v.ct[my + NT].w;
+                    }
+                    unsigned long long wk;
+                    const int wl = warp_argmax_lane(pk, &wk);
+                    const uint32_t wr = __shfl_sync(0xffffffffu, prec, wl);
+                    float4 cxyz = make_float4(0.f, 0.f, 0.f, 0.f);
+                    unsigned long long gbest;
+                    if (!CLUSTER) {
+                        // each warp publishes its candidate's key and coordinates (the record's owner
+                        // may rewrite its best point in the next iteration, before a slower warp reads it)
                         if (lane == 0) {
-                            const float srad = s_sxyz[g].w;
-                            s_skey[g] = gk;
-                            s_sxyz[g] = make_float4(bx, by, bz, srad);
-                            s_sct[g].w = prune_threshold(srad, gk);
+                            s_wkey[par][w] = wk;
+                            s_wxyz[par][w] = wk != 0ull ? (FAST ? v.best[wr] : s_sxyz[wr]) : make_float4(0.f, 0.f, 0.f, 0.f);
                         }
-                    }
-                    __syncthreads();
-                    // ---- D: my super-records' max
-                    pk = 0ull;
-                    prec = 0xffffffffu;
-                    for (uint32_t g = my; g < G; g += NT) {
-                        const unsigned long long kk = s_skey[g];
-                        if (kk > pk) {
-                            pk = kk;
-                            prec = g;
+                        __syncthreads();
+                        const unsigned long long ck = lane < NW ? s_wkey[par][lane] : 0ull;
+                        const int cl = warp_argmax_lane(ck, &gbest);
+                        cxyz = s_wxyz[par][cl];
+                    } else {
+                        // Every warp pushes its best (key, xyz) by st.async into slot [rank][warp] of every
+                        // CTA; each CTA's barrier for this round expects C * NW * 24 bytes.  (Reducing in the
+                        // CTA first and pushing one candidate per CTA has a lower isolated floor at 16 CTAs
+                        // but adds a CTA barrier after the record work, and measured slower in the kernel.)
+                        const uint32_t buf = it & 1u, ph = (it >> 1) & 1u;
+                        ++it;
+                        const uint32_t nslot = C * NW;
+                        if (t == 0) mbar_arrive_expect_tx(&s_mbar[buf], 24u * nslot);
+                        float4 wxyz = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (wk != 0ull && lane < static_cast<int>(C)) wxyz = FAST ? v.best[wr] : s_sxyz[wr];
+                        if (lane < static_cast<int>(C)) {
+                            const uint32_t rb = buf ? rbar1 : rbar0;
+                            st_async_u64(buf ? rkey1 : rkey0, wk, rb);
+                            st_async_f32x4(buf ? rxyz1 : rxyz0, wxyz, rb);
                         }
+                        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&s_mbar[buf], ph, kSpinLimit))) {
+                            if (lane == 0) atomicCAS(&a.hdr->status, 0u, kStatusTimeout);
+                            s_abort = 1;
+                            // the fast path has no CTA barrier per iteration: this warp leaves on its own,
+                            // and the other warps of the cluster time out in turn (each wait bounded)
+                            if (FAST) break;
+                        }
+                        unsigned long long kk = 0ull;
+                        uint32_t ki = 0;
+    #pragma unroll
+                        for (int u = 0; u < NSLOT / 32; ++u) {   // every slot, unrolled; unused ones read as 0
+                            const uint32_t q = static_cast<uint32_t>(u * 32 + lane);
+                            const unsigned long long x = q < nslot ? s_ckey[buf][q] : 0ull;
+                            if (x > kk) {
+                                kk = x;
+                                ki = q;
+                            }
+                        }
+                        const int gl = warp_argmax_lane(kk, &gbest);
+                        ki = __shfl_sync(0xffffffffu, ki, gl);
+                        cxyz = s_cxyz[buf][ki];
                     }
+                    sx = cxyz.x;
+                    sy = cxyz.y;
+                    sz = cxyz.z;
+                    if (rank == 0 && t == 0)
+                        a.out[c.out_off + (resume ? j - 1 : j)] = static_cast<int64_t>(key_index(gbest)) - c.pt_off;
+                    if (COUNTERS) ++cn.iter;
                 }
-                // ---- selection: warp -> CTA -> cluster
-                __syncwarp();
-                unsigned long long wk;
-                const int wl = warp_argmax_lane(pk, &wk);
-                const uint32_t wr = __shfl_sync(0xffffffffu, prec, wl);
-                float4 cxyz = make_float4(0.f, 0.f, 0.f, 0.f);
-                unsigned long long gbest;
-                if (!CLUSTER) {
-                    // each warp publishes its candidate's key and coordinates (the record's owner
-                    // may rewrite its best point in the next iteration, before a slower warp reads it)
-                    if (lane == 0) {
-                        s_wkey[par][w] = wk;
-                        s_wxyz[par][w] = wk != 0ull ? (fast ? v.best[wr] : s_sxyz[wr]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                    __syncthreads();
-                    const unsigned long long ck = lane < NW ? s_wkey[par][lane] : 0ull;
-                    const int cl = warp_argmax_lane(ck, &gbest);
-                    cxyz = s_wxyz[par][cl];
-                } else {
-                    // Every warp pushes its best (key, xyz) by st.async into slot [rank][warp] of every
-                    // CTA; each CTA's barrier for this round expects C * NW * 24 bytes.  (Reducing in the
-                    // CTA first and pushing one candidate per CTA has a lower isolated floor at 16 CTAs
-                    // but adds a CTA barrier after the record work, and measured slower in the kernel.)
-                    const uint32_t buf = it & 1u, ph = (it >> 1) & 1u;
-                    ++it;
-                    const uint32_t nslot = C * NW;
-                    if (t == 0) mbar_arrive_expect_tx(&s_mbar[buf], 24u * nslot);
-                    float4 wxyz = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (wk != 0ull && lane < static_cast<int>(C)) wxyz = fast ? v.best[wr] : s_sxyz[wr];
-                    if (lane < static_cast<int>(C)) {
-                        const uint32_t rb = buf ? rbar1 : rbar0;
-                        st_async_u64(buf ? rkey1 : rkey0, wk, rb);
-                        st_async_f32x4(buf ? rxyz1 : rxyz0, wxyz, rb);
-                    }
-                    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&s_mbar[buf], ph, kSpinLimit))) {
-                        if (lane == 0) atomicCAS(&a.hdr->status, 0u, kStatusTimeout);
-                        s_abort = 1;
-                        // the fast path has no CTA barrier per iteration: this warp leaves on its own,
-                        // and the other warps of the cluster time out in turn (each wait bounded)
-                        if (fast) break;
-                    }
-                    unsigned long long kk = 0ull;
-                    uint32_t ki = 0;
-#pragma unroll
-                    for (int u = 0; u < NSLOT / 32; ++u) {   // every slot, unrolled; unused ones read as 0
-                        const uint32_t q = static_cast<uint32_t>(u * 32 + lane);
-                        const unsigned long long x = q < nslot ? s_ckey[buf][q] : 0ull;
-                        if (x > kk) {
-                            kk = x;
-                            ki = q;
-                        }
-                    }
-                    const int gl = warp_argmax_lane(kk, &gbest);
-                    ki = __shfl_sync(0xffffffffu, ki, gl);
-                    cxyz = s_cxyz[buf][ki];
-                }
-                sx = cxyz.x;
-                sy = cxyz.y;
-                sz = cxyz.z;
-                if (rank == 0 && t == 0)
-                    a.out[c.out_off + (resume ? j - 1 : j)] = static_cast<int64_t>(key_index(gbest)) - c.pt_off;
-                if (COUNTERS) ++cn.iter;
-            }
+            };
+            if (!fast) iterate(IntC<0>{});
+            else if (NT <= 256 && nb <= 1) iterate(IntC<NT <= 256 ? 1 : 3>{});
+            else if (NT <= 256 && nb == 2) iterate(IntC<NT <= 256 ? 2 : 3>{});
+            else iterate(IntC<3>{});
             if (a.save_state) {
                 // state for a later resume: records kept in shared memory, resident points'
                 // distances, and the last selected sample (every CTA holds the same one)
