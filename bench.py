@@ -265,8 +265,17 @@ def run_batch64(args, rf, torch):
     clouds, desc = cloudgen.workload("batch64")
     sizes = [c.points.shape[0] for c in clouds]
     ms = [c.m for c in clouds]
-    opts = json.loads(args.opts) if args.opts else {"cluster": 8}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    tuned = None
+    if args.opts:
+        opts = json.loads(args.opts)
+    else:
+        # launch shape picked by the autotuner on this batch (cluster size, CTA threads, record
+        # chunk; the voxel resolution follows each cloud's size); every candidate gives the same indices
+        cat0 = torch.from_numpy(np.ascontiguousarray(np.concatenate([c.points for c in clouds]), np.float32)).cuda()
+        opts, table = rf.autotune.tune_batch(cat0, sizes, ms, reps=2)
+        tuned = [{"ms": round(t, 3), "opts": o} for t, o in table]
+        del cat0
     bs = rf.batch.BatchSampler(sizes, ms, opts=opts)
     bs.load([c.points for c in clouds])
     for _ in range(max(args.warmup, 3)):
@@ -296,7 +305,8 @@ def run_batch64(args, rf, torch):
     print(json.dumps({
         "metric": "clouds/s", "value": len(sizes) / (t_batch / 1e3), "unit": "clouds/s", "workload": "batch64",
         "desc": desc, "clouds": len(sizes), "points": int(sum(sizes)), "samples": int(sum(ms)),
-        "ms_per_batch": t_batch, "samples_per_s": sum(ms) / (t_batch / 1e3), "opts": opts, "graph": True,
+        "ms_per_batch": t_batch, "samples_per_s": sum(ms) / (t_batch / 1e3), "opts": opts, "autotune": tuned,
+        "graph": True,
         "gpu_launches_per_batch": launches,
         "per_cloud_launches": {"ms": t_sep, "clouds_per_s": len(sizes) / (t_sep / 1e3), "same_indices": same},
         "batched_vs_per_cloud": t_sep / t_batch, "plain_batched": plain}), flush=True)
