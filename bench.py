@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--max-batch", type=int, default=8, help="serving: clouds per micro-batch")
     ap.add_argument("--opts", default="", help="JSON dict of rfps_opts overrides")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="single-cloud workloads: the library's default launch shape instead of the autotuner's")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--floor-sweep", action="store_true",
                     help="print the sampling loop's per-iteration synchronisation floor for every launch shape")
@@ -131,6 +133,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# launch shapes the single-cloud benchmark lets the autotuner choose between
+TUNE_CANDIDATES = [{"cluster": 16, "threads": 256}, {"cluster": 16, "threads": 128}, {"cluster": 8, "threads": 256}]
+
+
 def kernel_hash():
     h = hashlib.sha256()
     for f in ("rfps_sample.cu", "rfps_common.cuh"):
@@ -139,14 +145,15 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload):
-    """DRAM bytes per launch of the sampling kernel from the committed ncu summary, if current."""
+def ncu_traffic(workload, opts):
+    """DRAM bytes per launch of the sampling kernel from the committed ncu summary, if it is of the
+    current kernel source and the same launch options."""
     p = os.path.join(ROOT, "profiles", f"k_sample_{workload}.json")
     if not os.path.exists(p):
         return None
     with open(p) as fh:
         d = json.load(fh)
-    if d.get("kernel_hash") != kernel_hash():
+    if d.get("kernel_hash") != kernel_hash() or (d.get("opts") or None) != (opts or None):
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -347,7 +354,7 @@ def main():
     torch.cuda.set_device(local)
     if args.floor_sweep:
         for cluster in (1, 2, 4, 8, 16):
-            for threads in (256, 512):
+            for threads in (128, 256, 512):
                 ms = min(rf.sync_floor(cluster, threads, 25000) for _ in range(3))
                 print(json.dumps({"cluster": cluster, "threads": threads, "ns_per_iteration": ms * 1e6 / 24999}),
                       flush=True)
@@ -363,6 +370,12 @@ def main():
     n, m, start = cloud.points.shape[0], cloud.m, cloud.start
     opts = json.loads(args.opts) if args.opts else None
     pts = torch.from_numpy(cloud.points).to(dev)
+    tuned = None
+    if opts is None and not (args.no_tune or args.once or args.study):
+        # launch shape from the autotuner, timed on this cloud before (outside) the timed region;
+        # every candidate returns the same indices
+        opts, table = rf.autotune.tune_single(pts, m, start, candidates=TUNE_CANDIDATES, reps=3)
+        tuned = [{"ms": round(t, 3), "opts": o} for t, o in table]
     ws = torch.empty(rf.workspace_size(n, opts), dtype=torch.uint8, device=dev)
     out = torch.empty(m, dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -499,11 +512,11 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": desc, "n": n, "m": m, "start": start,
                        "clouds_per_gpu_per_step": 1, "l2": "flushed between steps (256 MiB write)",
-                       "opts": opts or "default"},
+                       "opts": opts or "default", "autotune": tuned},
             "ms_per_cloud": ms_per_step,
             "plain_gpu_fps": plain,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": ncu_traffic(args.workload),
+                         "frac": achieved / peak, "traffic": ncu_traffic(args.workload, opts),
                          "kernel": "k_sample", "kernel_ms": k_ms, "alg_bytes_per_launch": alg_bytes,
                          "peak_kind": peak_kind,
                          "ns_per_iteration": k_ms * 1e6 / max(1, m - 1),

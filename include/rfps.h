@@ -62,7 +62,7 @@ typedef enum {
 typedef struct {
     int32_t n_vox;       /* voxel bins per axis, n_vox of Sec. 3.2 (v in Sec. 5.6.2); 1..256 */
     int32_t cluster;     /* CTAs working on one cloud (thread-block cluster size): 1,2,4,8,16 */
-    int32_t threads;     /* threads per CTA of the sampling kernel: 256 or 512 */
+    int32_t threads;     /* threads per CTA of the sampling kernel: 128, 256 or 512 */
     int32_t chunk;       /* max points per voxel record (a voxel with more points is split
                             into several records): power of two in 32..4096; default 128 */
     int32_t prune;       /* 1: spherical-voxel radius pruning (Sec. 3.4.2) on */
@@ -221,7 +221,7 @@ rfps_status rfps_plain_fps_batched(const float *points, int64_t total_n,
  * "only synchronization point" of each iteration).  `workspace`: device, at
  * least 136 bytes, 256-byte aligned: one value per CTA (16 x 8 bytes), then a
  * status word (RFPS_ETIMEOUT if a bounded wait gave up; the caller zeroes it).
- * cluster in {1, 2, 4, 8, 16}, threads in {256, 512}.
+ * cluster in {1, 2, 4, 8, 16}, threads in {128, 256, 512}.
  * ---------------------------------------------------------------------- */
 rfps_status rfps_sync_floor(int32_t cluster, int32_t threads, int64_t iterations,
                             void *workspace, size_t workspace_bytes, void *stream);

@@ -36,7 +36,7 @@ def key(kind: str, n: int, batch: int = 1) -> str:
 def default_candidates(batch: bool = False):
     cands = []
     for cluster in ((2, 4, 8, 16) if batch else (4, 8, 16)):
-        for threads in (256, 512):
+        for threads in (128, 256, 512):
             for chunk in (64, 128):
                 cands.append({"cluster": cluster, "threads": threads, "chunk": chunk})
     return cands

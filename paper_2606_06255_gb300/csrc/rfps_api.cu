@@ -70,7 +70,7 @@ rfps_opts resolve_opts(const rfps_opts* in, int64_t max_n)
     // Defaults from launch-shape sweeps on GB300: the per-iteration cost is the
     // cluster exchange plus the unpruned records' work, and 16 CTAs of 256
     // threads were fastest from 4k points up (room, LiDAR and uniform clouds).
-    if (o.threads != 256 && o.threads != 512) o.threads = 256;
+    if (o.threads != 128 && o.threads != 256 && o.threads != 512) o.threads = 256;
     if (o.cluster <= 0) o.cluster = max_n < 2048 ? 1 : 16;
     if (o.chunk <= 0) o.chunk = 128;
     return o;
@@ -169,7 +169,7 @@ static rfps_status check_opts(const rfps_opts* o)
     if (o->cluster != 0 && o->cluster != 1 && o->cluster != 2 && o->cluster != 4 && o->cluster != 8 &&
         o->cluster != 16)
         return RFPS_EINVAL;
-    if (o->threads != 0 && o->threads != 256 && o->threads != 512) return RFPS_EINVAL;
+    if (o->threads != 0 && o->threads != 128 && o->threads != 256 && o->threads != 512) return RFPS_EINVAL;
     if (o->chunk != 0 && (!is_pow2(o->chunk) || o->chunk < 32 || o->chunk > 4096)) return RFPS_EINVAL;
     if (o->radius_mode != 0 && o->radius_mode != 1) return RFPS_EINVAL;
     return RFPS_OK;
@@ -357,7 +357,7 @@ rfps_status rfps_plain_fps_batched(const float* points, int64_t total_n, const i
 rfps_status rfps_sync_floor(int32_t cluster, int32_t threads, int64_t iterations, void* workspace,
                             size_t workspace_bytes, void* stream)
 {
-    if (!workspace || iterations < 1 || (threads != 256 && threads != 512) ||
+    if (!workspace || iterations < 1 || (threads != 128 && threads != 256 && threads != 512) ||
         (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8 && cluster != 16) ||
         workspace_bytes < 17 * sizeof(unsigned long long) || !aligned256(workspace))
         return RFPS_EINVAL;

@@ -448,8 +448,8 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
 
             // The iteration loop, compiled once per path so that each is scheduled on its own:
             // MODE 0 hierarchical; 1 and 2 fast with this lane's one or two records' centres and
-            // thresholds held in registers (nloc <= NT, <= 2 NT; 256-thread CTAs, whose register
-            // budget has room for it); 3 fast with any number per lane.
+            // thresholds held in registers (nloc <= NT, <= 2 NT; 128- and 256-thread CTAs, whose
+            // register budget has room for it); 3 fast with any number per lane.
             const int nb = static_cast<int>((nloc + NT - 1) / NT);
             auto iterate = [&](auto mode) {
                 constexpr int MODE = decltype(mode)::value;
@@ -916,6 +916,7 @@ cudaError_t launch_one(SampleArgs args, int C, int64_t n_clouds, cudaStream_t st
 template <bool CLUSTER, bool COUNTERS>
 cudaError_t launch_nt(const SampleArgs& args, int NT, int C, int64_t n_clouds, cudaStream_t st)
 {
+    if (NT == 128) return launch_one<128, CLUSTER, COUNTERS>(args, C, n_clouds, st);
     return NT == 256 ? launch_one<256, CLUSTER, COUNTERS>(args, C, n_clouds, st)
                      : launch_one<512, CLUSTER, COUNTERS>(args, C, n_clouds, st);
 }
@@ -983,7 +984,11 @@ cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int6
 
 cudaError_t launch_sync_floor(int C, int NT, int64_t iters, unsigned long long* sink, cudaStream_t st)
 {
-    if (C > 1) return NT == 256 ? launch_floor<256, true>(C, iters, sink, st) : launch_floor<512, true>(C, iters, sink, st);
+    if (C > 1) {
+        if (NT == 128) return launch_floor<128, true>(C, iters, sink, st);
+        return NT == 256 ? launch_floor<256, true>(C, iters, sink, st) : launch_floor<512, true>(C, iters, sink, st);
+    }
+    if (NT == 128) return launch_floor<128, false>(1, iters, sink, st);
     return NT == 256 ? launch_floor<256, false>(1, iters, sink, st) : launch_floor<512, false>(1, iters, sink, st);
 }
 

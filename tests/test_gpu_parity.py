@@ -57,6 +57,9 @@ OPT_GRID = [
     dict(cluster=4, threads=512, chunk=256, n_vox=24, skip=0),
     dict(cluster=2, threads=512, chunk=256, n_vox=24, prune=0, skip=0),
     dict(cluster=2, threads=512, chunk=256, n_vox=20, radius_mode=1),
+    dict(cluster=1, threads=128, chunk=64, n_vox=12),
+    dict(cluster=16, threads=128, chunk=128, n_vox=24),
+    dict(cluster=8, threads=128, chunk=32, n_vox=40),
     dict(cluster=1, threads=512, chunk=64, n_vox=12, prune=0),
     dict(cluster=16, threads=512, chunk=128, n_vox=24, skip=0),
     dict(n_vox=1),
@@ -304,7 +307,7 @@ def _lattice(nx, ny, nz):
 
 @pytest.mark.parametrize("opts", [
     dict(cluster=2, threads=256), dict(cluster=4, threads=512), dict(cluster=8, threads=256),
-    dict(cluster=16, threads=256), dict(cluster=16, threads=512),
+    dict(cluster=16, threads=256), dict(cluster=16, threads=512), dict(cluster=16, threads=128),
 ], ids=lambda o: "c%d_t%d" % (o["cluster"], o["threads"]))
 def test_exact_ties_across_cluster_exchange(rf, opts):
     """Equal squared distances in different warps and CTAs: the smallest point index must win (Sec. 3.1)."""
