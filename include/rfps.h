@@ -82,6 +82,10 @@ typedef struct {
     uint64_t points_skipped;  /* points dropped by Eq. point_skip_condition */
     uint64_t points_updated;  /* strict decreases of a stored distance (effective updates) */
     uint64_t iterations;      /* sampling iterations (selections after the start point) */
+    uint64_t prune_violations; /* shadow check: points of pruned records whose distance to the
+                                  new sample was below their stored one (0 when the bound is safe) */
+    uint64_t skip_violations;  /* shadow check: skipped points whose distance to the new sample was
+                                  below their stored one (0 when the skip is exact) */
 } rfps_counters;
 
 /* Fills *opts with the defaults (all automatic, prune = skip = 1). */

@@ -390,6 +390,8 @@ rfps_status rfps_counters_read(const void* workspace, rfps_counters* out, void* 
     out->points_skipped = h.counters[3];
     out->points_updated = h.counters[4];
     out->iterations = h.counters[5];
+    out->prune_violations = h.counters[6];
+    out->skip_violations = h.counters[7];
     return RFPS_OK;
 }
 

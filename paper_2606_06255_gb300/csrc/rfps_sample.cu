@@ -77,7 +77,21 @@ struct RecView {
 
 struct Cnt {
     uint64_t tests = 0, pruned = 0, visit = 0, skip = 0, upd = 0, iter = 0;
+    uint64_t pviol = 0, sviol = 0;   // shadow checks: see shadow_pruned and the skip branch below
 };
+
+// Counting runs only: the points of a record the bound pruned are checked
+// against the new sample s anyway.  A distance that would strictly decrease
+// means the prune bound was not safe for that record (must never happen).
+__device__ uint64_t shadow_pruned(const float4* pts, uint32_t off, uint32_t cnt, float sx, float sy, float sz)
+{
+    uint64_t v = 0;
+    for (uint32_t q = 0; q < cnt; ++q) {
+        const float4 p = pts[off + q];
+        if (sq_dist(p.x, p.y, p.z, sx, sy, sz) < p.w) ++v;
+    }
+    return v;
+}
 
 // One warp updates the points [off, off + cnt) of a record against s (point
 // skip, strict update, d2 write-back) and returns the lane's max key; the
@@ -112,7 +126,10 @@ __device__ __forceinline__ unsigned long long visit_points(float4* pts, const ui
                 const float xx = __fmul_rn(dx, dx), yy = __fmul_rn(dy, dy), zz = __fmul_rn(dz, dz);
                 bool write = first;
                 if (skip && skip_point(xx, yy, zz, d2)) {
-                    if (COUNTERS) ++k.skip;
+                    if (COUNTERS) {
+                        ++k.skip;
+                        if (__fadd_rn(__fadd_rn(xx, yy), zz) < d2) ++k.sviol;   // the skip was not exact
+                    }
                 } else {
                     const float nd = __fadd_rn(__fadd_rn(xx, yy), zz);
                     if (nd < d2) {
@@ -155,7 +172,10 @@ __device__ __forceinline__ unsigned long long visit_points_smem(float4* pts, con
         const float xx = __fmul_rn(dx, dx), yy = __fmul_rn(dy, dy), zz = __fmul_rn(dz, dz);
         bool write = first;
         if (skip && skip_point(xx, yy, zz, d2)) {
-            if (COUNTERS) ++k.skip;
+            if (COUNTERS) {
+                ++k.skip;
+                if (__fadd_rn(__fadd_rn(xx, yy), zz) < d2) ++k.sviol;   // the skip was not exact
+            }
         } else {
             const float nd = __fadd_rn(__fadd_rn(xx, yy), zz);
             if (nd < d2) {
@@ -456,6 +476,12 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                 constexpr bool FAST = MODE != 0;
                 constexpr int NREG = MODE == 1 || MODE == 2 ? MODE : 0;
                 float4 ct0 = make_float4(0.f, 0.f, 0.f, 0.f), ct1 = ct0;
+                // counting runs: the shadow check of a pruned record held by this CTA
+                auto shadow_record = [&](uint32_t l) -> uint64_t {
+                    const uint2 rg = v.rng[l];
+                    return (resident && (rg.x & kResident)) ? shadow_pruned(s_pts, rg.x & ~kResident, rg.y, sx, sy, sz)
+                                                            : shadow_pruned(a.pts4, rg.x, rg.y, sx, sy, sz);
+                };
                 if constexpr (NREG > 0) {
                     if (my < nloc) ct0 = v.ct[my];
                     if (NREG == 2 && my + NT < nloc) ct1 = v.ct[my + NT];
@@ -477,6 +503,8 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             if (COUNTERS && !first) {
                                 cn.tests += (h0 ? 1 : 0) + (h1 ? 1 : 0);
                                 cn.pruned += (h0 && !k0 ? 1 : 0) + (h1 && !k1 ? 1 : 0);
+                                if (h0 && !k0) cn.pviol += shadow_record(my);
+                                if (h1 && !k1) cn.pviol += shadow_record(my + NT);
                             }
                         } else {
                             for (int b = 0; b < nb; ++b) {
@@ -487,6 +515,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                                     if (COUNTERS && !first) {
                                         ++cn.tests;
                                         cn.pruned += keep ? 0 : 1;
+                                        if (!keep) cn.pviol += shadow_record(l);
                                     }
                                 }
                             }
@@ -582,6 +611,12 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                                 if (COUNTERS && !first) {
                                     ++cn.tests;
                                     cn.pruned += keep ? 0 : 1;
+                                    if (!keep) {   // every record of the pruned super-record
+                                        for (uint32_t l = g * 32; l < min(nloc, g * 32 + 32); ++l) {
+                                            const uint2 rg = a.rec_rng[v.g(l)];
+                                            cn.pviol += shadow_pruned(a.pts4, rg.x, rg.y, sx, sy, sz);
+                                        }
+                                    }
                                 }
                             }
                             const uint32_t nkeep = __popc(su);
@@ -626,6 +661,10 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                                 if (COUNTERS && !first) {
                                     ++cn.tests;
                                     cn.pruned += keep ? 0 : 1;
+                                    if (!keep && a.prune) {
+                                        const uint2 rg = a.rec_rng[v.g(l)];
+                                        cn.pviol += shadow_pruned(a.pts4, rg.x, rg.y, sx, sy, sz);
+                                    }
                                 }
                             }
                             uint32_t mask = __ballot_sync(0xffffffffu, keep);
@@ -793,6 +832,8 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[3]), cn.skip);
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[4]), cn.upd);
         if (t == 0 && rank == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[5]), cn.iter);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[6]), cn.pviol);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[7]), cn.sviol);
     }
 }
 

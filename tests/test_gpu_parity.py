@@ -247,6 +247,34 @@ def test_counters(rf):
     assert c["points_visited"] < 0.2 * 50000 * 4999
 
 
+SHADOW_CASES = [
+    ("room_20k_c16_t128", lambda: cloudgen.room_cloud(20000, seed=81), 3000, {"cluster": 16, "threads": 128}),
+    ("room_20k_c1", lambda: cloudgen.room_cloud(20000, seed=82), 3000, {"cluster": 1}),
+    ("lidar_30k_c4", lambda: cloudgen.lidar_cloud(30000, seed=83), 3000, {"cluster": 4, "threads": 512}),
+    ("lattice_ties_c8", lambda: _lattice(20, 20, 20), 2000, {"cluster": 8}),
+    ("wide_scale_c16", lambda: cloudgen.uniform_cloud(8000, seed=84) * np.float32(3e12), 1500, {"cluster": 16}),
+    ("tiny_scale_c2", lambda: cloudgen.uniform_cloud(8000, seed=85) * np.float32(1e-15), 1500, {"cluster": 2}),
+    ("duplicates_c16", lambda: cloudgen.uniform_cloud(500, seed=86)[np.random.default_rng(87).integers(0, 500, 6000)],
+     1000, {"cluster": 16}),
+    ("hierarchical_c1", lambda: cloudgen.uniform_cloud(60000, seed=88), 300, {"cluster": 1, "chunk": 32, "n_vox": 40}),
+]
+
+
+@pytest.mark.parametrize("name,make,m,opts", SHADOW_CASES, ids=[c[0] for c in SHADOW_CASES])
+def test_shadow_checks_find_no_unsafe_prune_or_skip(rf, name, make, m, opts):
+    """Counting runs also check every pruned record's points and every skipped point against the new
+    sample: no stored distance may be due for a strict decrease there, so the FP32 radius bound
+    (Eq. radius_pruning_condition) and the coordinate skip (Eq. point_skip_condition) lose nothing."""
+    pts = make().astype(np.float32)
+    o = dict(opts, counters=1)
+    ws = torch.empty(rf.workspace_size(pts.shape[0], o), dtype=torch.uint8, device="cuda")
+    out = rf.fps(dev(pts), m, 0, opts=o, workspace=ws)
+    c = rf.counters(ws)
+    np.testing.assert_array_equal(out.cpu().numpy(), oracle.fps(pts, m, 0, threads=0))
+    assert c["voxels_pruned"] > 0 and c["points_skipped"] > 0
+    assert c["prune_violations"] == 0 and c["skip_violations"] == 0, c
+
+
 def test_launch_counter_moves(rf):
     before = rf.launch_count()
     gpu_fps(rf, cloudgen.uniform_cloud(500, seed=1), 50)
