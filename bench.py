@@ -146,7 +146,8 @@ class ClockSampler:
 
 
 # launch shapes the single-cloud benchmark lets the autotuner choose between
-TUNE_CANDIDATES = [{"cluster": 16, "threads": 256}, {"cluster": 16, "threads": 128}, {"cluster": 8, "threads": 256}]
+TUNE_CANDIDATES = [{"cluster": 16, "threads": 256}, {"cluster": 16, "threads": 128}, {"cluster": 8, "threads": 256},
+                   {"cluster": 16, "threads": 256, "chunk": 256}]
 
 
 def kernel_hash():

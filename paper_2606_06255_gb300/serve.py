@@ -14,6 +14,15 @@ cloud alone: every cloud's indices depend only on its own points.
 The GPU work sits behind a small executor interface (mem_needed / launch /
 done / results) so the scheduling logic can be exercised on the CPU with a
 simulated executor.
+
+Failures degrade service instead of stopping it: a micro-batch whose launch
+raises (an allocation or API error) or whose results report a device error
+(a timed-out wait, a non-finite coordinate) releases its slot and memory,
+and its requests are queued again: from a batch of several each runs alone
+next (so one bad request cannot take its batch-mates down), and a request
+that fails on its own is retried up to `max_retries` times, then reported
+as failed.  A request may carry a queueing deadline (dropped as expired if
+not admitted in time) and a cancellation time (dropped if still queued then).
 """
 
 from __future__ import annotations
@@ -33,6 +42,9 @@ class Request:
     points: np.ndarray      # (N, 3) float32 (or a pinned host tensor)
     m: int
     start: int = 0
+    deadline: float | None = None    # seconds after arrival by which it must be admitted
+    cancel_at: float | None = None   # the client withdraws it at this time if still queued
+    attempts: int = 0                # launches that failed so far
 
 
 @dataclass
@@ -52,7 +64,10 @@ class Completed:
 @dataclass
 class Report:
     completed: list = field(default_factory=list)
-    rejected: list = field(default_factory=list)
+    rejected: list = field(default_factory=list)     # can never fit the memory budget
+    failed: list = field(default_factory=list)       # (rid, reason) after the retries ran out
+    expired: list = field(default_factory=list)      # not admitted before their deadline
+    cancelled: list = field(default_factory=list)    # withdrawn while queued
     makespan: float = 0.0
     offered_rate: float = 0.0
     window: tuple = (0.0, 0.0)       # first and last arrival
@@ -72,6 +87,9 @@ class Report:
             "steady_clouds_per_s": steady / (b - a) if b > a else None,
             "requests_completed": n,
             "requests_rejected": len(self.rejected),
+            "requests_failed": len(self.failed),
+            "requests_expired": len(self.expired),
+            "requests_cancelled": len(self.cancelled),
             "offered_clouds_per_s": self.offered_rate,
             "achieved_clouds_per_s": n / self.makespan if self.makespan > 0 else None,
             "p50_latency_ms": 1e3 * q(0.50) if lat else None,
@@ -86,14 +104,15 @@ class Report:
 
 class Server:
     def __init__(self, executor, mem_budget: int, max_inflight: int = 4, max_batch: int = 16,
-                 poll_s: float = 2e-4):
-        if max_inflight < 1 or max_batch < 1 or mem_budget <= 0:
+                 poll_s: float = 2e-4, max_retries: int = 1):
+        if max_inflight < 1 or max_batch < 1 or mem_budget <= 0 or max_retries < 0:
             raise ValueError("bad server limits")
         self.ex = executor
         self.budget = int(mem_budget)
         self.max_inflight = int(max_inflight)
         self.max_batch = int(max_batch)
         self.poll_s = poll_s
+        self.max_retries = int(max_retries)
 
     def run(self, requests, clock=time.perf_counter, sleep=time.sleep) -> Report:
         reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
@@ -109,6 +128,22 @@ class Server:
         free_slots = list(range(self.max_inflight))[::-1]
         mem_used = 0
         last_finish = 0.0
+        alone = set()            # rids that run in a batch of their own after a batch failure
+
+        def requeue(batch, reason):
+            # a failed micro-batch: its requests go back to the head of the queue to run alone; one
+            # that failed alone spends a retry, and fails for good when they run out
+            for r in reversed(batch):
+                if len(batch) > 1:
+                    alone.add(r.rid)
+                    queue.appendleft(r)
+                    continue
+                r.attempts += 1
+                if r.attempts > self.max_retries:
+                    rep.failed.append((r.rid, reason))
+                else:
+                    queue.appendleft(r)
+
         while i < len(reqs) or queue or inflight:
             now = clock() - t0
             progressed = False
@@ -116,13 +151,30 @@ class Server:
                 queue.append(reqs[i])
                 i += 1
                 progressed = True
+            if any(r.deadline is not None or r.cancel_at is not None for r in queue):
+                keep = collections.deque()
+                for r in queue:
+                    if r.cancel_at is not None and now >= r.cancel_at:
+                        rep.cancelled.append(r.rid)
+                    elif r.deadline is not None and now > r.arrival + r.deadline:
+                        rep.expired.append(r.rid)
+                    else:
+                        keep.append(r)
+                progressed = progressed or len(keep) != len(queue)
+                queue = keep
             for slot in list(inflight):
                 handle, batch, t_adm, mem = inflight[slot]
                 if self.ex.done(handle):
                     t_done = clock() - t0
-                    for r, idx in zip(batch, self.ex.results(handle)):
-                        rep.completed.append(Completed(r.rid, r.arrival, t_adm, t_done, len(batch), idx))
-                    last_finish = max(last_finish, t_done)
+                    try:
+                        results = self.ex.results(handle)
+                    except Exception as e:   # a device error reported with the results
+                        results = None
+                        requeue(batch, f"results: {e}")
+                    if results is not None:
+                        for r, idx in zip(batch, results):
+                            rep.completed.append(Completed(r.rid, r.arrival, t_adm, t_done, len(batch), idx))
+                        last_finish = max(last_finish, t_done)
                     mem_used -= mem
                     free_slots.append(slot)
                     del inflight[slot]
@@ -135,6 +187,8 @@ class Server:
                     continue
                 batch = []
                 while queue and len(batch) < self.max_batch:
+                    if batch and (queue[0].rid in alone or batch[0].rid in alone):
+                        break
                     need = self.ex.mem_needed(batch + [queue[0]])
                     if mem_used + need > self.budget:
                         break
@@ -143,7 +197,14 @@ class Server:
                     break                                        # wait for memory to free up
                 need = self.ex.mem_needed(batch)
                 slot = free_slots.pop()
-                inflight[slot] = (self.ex.launch(batch, slot), batch, clock() - t0, need)
+                try:
+                    handle = self.ex.launch(batch, slot)
+                except Exception as e:       # allocation or API error: the slot stays free
+                    free_slots.append(slot)
+                    requeue(batch, f"launch: {e}")
+                    progressed = True
+                    break
+                inflight[slot] = (handle, batch, clock() - t0, need)
                 mem_used += need
                 rep.peak_mem = max(rep.peak_mem, mem_used)
                 rep.max_inflight_batches = max(rep.max_inflight_batches, len(inflight))
@@ -229,12 +290,16 @@ class GpuExecutor:
             ev.record(s)
         ooff = np.concatenate([[0], np.cumsum(ms)])
         # keep every buffer alive until the event completes
-        return {"event": ev, "host_out": host_out, "ooff": ooff, "keep": (meta, dmeta, pts, ws, out, staged)}
+        return {"event": ev, "host_out": host_out, "ooff": ooff, "ws": ws, "stream": s,
+                "keep": (meta, dmeta, pts, ws, out, staged)}
 
     def done(self, handle) -> bool:
         return handle["event"].query()
 
     def results(self, handle):
+        st = self.lib.status(handle["ws"], handle["stream"])   # the launch has completed: no wait
+        if st != 0:
+            raise RuntimeError(f"device status {st}")
         o, ooff = handle["host_out"].numpy(), handle["ooff"]
         return [o[ooff[b]:ooff[b + 1]].copy() for b in range(len(ooff) - 1)]
 

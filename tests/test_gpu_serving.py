@@ -77,3 +77,22 @@ def test_autotune_picks_a_candidate_with_identical_results(rf, tmp_path):
     assert rf.autotune.best_opts("room", 20000, path=path) == best
     got = rf.fps(pts, 4000, 0, opts=best, check=True).cpu().numpy()
     np.testing.assert_array_equal(got, oracle.fps(pts_np, 4000, 0, threads=0))
+
+
+def test_device_error_fails_only_the_bad_request(rf):
+    """A cloud with a non-finite coordinate makes its micro-batch report RFPS_ENONFINITE on the device:
+    the server reruns that batch's clouds one by one, serves the others and reports the bad one."""
+    clouds = _mixed(6, 1300)
+    bad = clouds[2].copy()
+    bad[17, 1] = np.nan
+    clouds[2] = bad
+    reqs = [rf.serve.Request(i, 0.0, c, max(1, c.shape[0] // 16), 0) for i, c in enumerate(clouds)]
+    ex = rf.serve.GpuExecutor(n_slots=2, opts={"cluster": 2})
+    rep = rf.serve.Server(ex, mem_budget=1 << 30, max_inflight=2, max_batch=6, max_retries=1).run(reqs)
+    assert [rid for rid, _ in rep.failed] == [2]
+    assert "device status" in rep.failed[0][1]
+    by_id = {c.rid: c for c in rep.completed}
+    assert sorted(by_id) == [0, 1, 3, 4, 5]
+    for r in reqs:
+        if r.rid in by_id:
+            np.testing.assert_array_equal(by_id[r.rid].indices, oracle.fps(r.points, r.m, r.start, threads=0))

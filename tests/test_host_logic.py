@@ -93,6 +93,67 @@ def test_scheduler_admits_by_memory_and_rejects_oversize():
     assert rep.peak_mem <= 2_500_000
 
 
+class FlakyExecutor(SimExecutor):
+    """Launches fail (an allocation error) or report a device error on chosen requests."""
+
+    def __init__(self, clock, launch_fail, result_fail, **kw):
+        super().__init__(clock, **kw)
+        self.launch_fail = dict(launch_fail)     # rid -> failing launches left
+        self.result_fail = dict(result_fail)
+
+    def launch(self, batch, slot):
+        for r in batch:
+            if self.launch_fail.get(r.rid, 0) > 0:
+                self.launch_fail[r.rid] -= 1
+                raise MemoryError("simulated allocation failure")
+        h = super().launch(batch, slot)
+        h["bad"] = any(self.result_fail.get(r.rid, 0) > 0 for r in batch)
+        for r in batch:
+            if self.result_fail.get(r.rid, 0) > 0:
+                self.result_fail[r.rid] -= 1
+        return h
+
+    def results(self, h):
+        if h["bad"]:
+            raise RuntimeError("device status 5")
+        return super().results(h)
+
+
+def test_failed_batches_are_retried_then_reported():
+    clk = FakeClock()
+    reqs = _requests(30, rate=3000.0, seed=11)
+    # rid 3: one failed launch (retried, then served); rid 7: launches always fail; rid 12: one
+    # device error (retried); rid 20: device errors every time
+    ex = FlakyExecutor(clk, launch_fail={3: 1, 7: 99}, result_fail={12: 1, 20: 99})
+    rep = serve.Server(ex, mem_budget=10**9, max_inflight=3, max_batch=4, max_retries=2).run(
+        reqs, clock=clk, sleep=clk.sleep)
+    failed = {rid for rid, _ in rep.failed}
+    assert failed == {7, 20}
+    assert all("launch" in why for rid, why in rep.failed if rid == 7)
+    assert all("results" in why for rid, why in rep.failed if rid == 20)
+    done = {c.rid: c for c in rep.completed}
+    assert set(done) == {r.rid for r in reqs} - failed   # batch-mates of failing requests are served too
+    for r in reqs:
+        if r.rid in done:
+            np.testing.assert_array_equal(done[r.rid].indices, oracle.fps(r.points, r.m, r.start))
+    assert rep.summary()["requests_failed"] == 2
+
+
+def test_deadlines_and_cancellation_while_queued():
+    clk = FakeClock()
+    ex = SimExecutor(clk, per_sample_s=2e-4)         # slow: the queue builds up behind one slot
+    reqs = _requests(12, rate=10000.0, seed=13)
+    reqs[5].deadline = 1e-3                          # cannot be admitted that soon
+    reqs[8].cancel_at = reqs[8].arrival + 1e-4       # withdrawn while still queued
+    reqs[10].deadline = 1e3                          # generous: served
+    rep = serve.Server(ex, mem_budget=10**9, max_inflight=1, max_batch=1).run(reqs, clock=clk, sleep=clk.sleep)
+    assert rep.expired == [5] and rep.cancelled == [8]
+    done = {c.rid for c in rep.completed}
+    assert done == {r.rid for r in reqs} - {5, 8}
+    s = rep.summary()
+    assert s["requests_expired"] == 1 and s["requests_cancelled"] == 1
+
+
 def test_assignment_balances_and_covers():
     sizes = [8000, 200000, 50000, 12000, 90000, 30000, 150000, 9000]
     ms = [n // 4 for n in sizes]
