@@ -4,8 +4,8 @@
 // Pipeline (one stream, every cloud of a batch at once):
 //   k_setup      cloud table, device checks of the caller's arrays, n_vox per
 //                cloud, global cell numbering, largest-first cloud order
-//   k_bbox       bounding box per cloud + non-finite detection        (Alg. 2 l.1)
-//   k_grid       L = alpha * max(E) / n_vox  (Eq. voxel_size)          (Alg. 2 l.2)
+//   k_bbox       bounding box per cloud + non-finite detection        (Alg. 2, bounds)
+//   k_grid       L = alpha * max(E) / n_vox  (Eq. voxel_size)          (Alg. 2, voxel size)
 //   k_bin        clamped floor binning (Alg. 2 Phase 1); the sort key is the cell's Morton
 //                code rather than v_z n^2 + v_y n + v_x, so sorted neighbours are 3-D compact
 //   radix sort   stable LSD sort of (global cell id, point index)      (Alg. 2 sort)
