@@ -277,6 +277,15 @@ rfps_status rfps_index_sample(rfps_index *index, int64_t m, int64_t start,
  * would exceed N.  One sequence per index at a time (stream-ordered). */
 rfps_status rfps_index_sample_more(rfps_index *index, int64_t m_more,
                                    int64_t *out_idx, void *stream);
+/* rfps_index_distances: the FPS state of the current sequence, Alg. 1's D:
+ * every point's FP32 squared distance (canonical arithmetic) to the samples
+ * whose update has been applied, i.e. all but the last sample taken (its
+ * update opens the next rfps_index_sample_more).  Written to the DEVICE
+ * array d2_out[n] in the caller's point order, stream-ordered on `stream`
+ * after the sampling calls there.  RFPS_EINVAL before the first
+ * rfps_index_sample. */
+rfps_status rfps_index_distances(const rfps_index *index, float *d2_out,
+                                 void *stream);
 size_t rfps_index_bytes(const rfps_index *index);
 void rfps_index_free(rfps_index *index);
 rfps_status rfps_index_export(const rfps_index *index, int64_t *n_records,

@@ -84,6 +84,7 @@ def _load():
         "rfps_index_build": (st, [vp, i64, optp, ctypes.POINTER(vp), vp]),
         "rfps_index_sample": (st, [vp, i64, i64, vp, vp]),
         "rfps_index_sample_more": (st, [vp, i64, vp, vp]),
+        "rfps_index_distances": (st, [vp, vp, vp]),
         "rfps_index_bytes": (sz, [vp]),
         "rfps_index_free": (None, [vp]),
         "rfps_index_export": (st, [vp, ctypes.POINTER(i64), vp, vp, vp, vp, vp, vp, ctypes.POINTER(i32)]),
@@ -316,6 +317,14 @@ class Index:
         _check(_lib.rfps_index_sample_more(self._h, m_more, out.data_ptr(), _stream(stream)),
                "rfps_index_sample_more")
         return out
+
+    def distances(self, stream=None) -> torch.Tensor:
+        """Every point's FP32 squared distance to the samples applied so far (all but the last)."""
+        if self._h is None:
+            raise RuntimeError("index freed")
+        d2 = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        _check(_lib.rfps_index_distances(self._h, d2.data_ptr(), _stream(stream)), "rfps_index_distances")
+        return d2
 
     def export(self) -> dict:
         n = self.n

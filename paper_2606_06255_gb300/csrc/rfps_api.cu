@@ -45,6 +45,14 @@ __global__ void k_rearm(WsHeader* hdr, CloudDev* clouds, int64_t m, int64_t star
     clouds[0].resume = resume;
 }
 
+// Each point's stored distance (sorted position i, .w of the float4) back to its original row.
+__global__ void k_index_d2(const float4* pts4, const uint32_t* porig, int64_t n, float* d2)
+{
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        d2[porig[i]] = pts4[i].w;
+}
+
 rfps_status from_cuda(cudaError_t e) { return e == cudaSuccess ? RFPS_OK : RFPS_ECUDA; }
 
 rfps_status device_check()
@@ -462,6 +470,18 @@ rfps_status rfps_index_sample_more(rfps_index* ix, int64_t m_more, int64_t* out_
     }
     ix->taken += m_more;
     return RFPS_OK;
+}
+
+rfps_status rfps_index_distances(const rfps_index* ix, float* d2_out, void* stream)
+{
+    if (!ix || !d2_out || ix->taken < 1) return RFPS_EINVAL;
+    const char* ws = static_cast<const char*>(ix->mem);
+    const int64_t blocks = std::min<int64_t>((ix->n + 255) / 256, 4096);
+    k_index_d2<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const float4*>(ws + ix->L.pts4), reinterpret_cast<const uint32_t*>(ws + ix->L.porig), ix->n,
+        d2_out);
+    note_launches(1);
+    return from_cuda(cudaGetLastError());
 }
 
 size_t rfps_index_bytes(const rfps_index* ix) { return ix ? ix->bytes : 0; }

@@ -354,3 +354,34 @@ def test_exact_ties_hierarchical_cluster(rf):
     grid = _lattice(64, 64, 48)
     ref = oracle.fps(grid, 3000, 5, threads=0)
     np.testing.assert_array_equal(gpu_fps(rf, grid, 3000, 5, cluster=2, n_vox=64, chunk=32), ref)
+
+
+D2_CASES = [
+    ("room_20k_c16_t128", lambda: cloudgen.room_cloud(20000, seed=91), {"cluster": 16, "threads": 128}),
+    ("lidar_30k_c4", lambda: cloudgen.lidar_cloud(30000, seed=92), {"cluster": 4}),
+    ("lattice_ties_c8", lambda: _lattice(16, 16, 16), {"cluster": 8}),
+    ("partly_resident_c1", lambda: cloudgen.lidar_cloud(40000, seed=93), {"cluster": 1, "threads": 512}),
+    ("hierarchical_c1", lambda: cloudgen.uniform_cloud(60000, seed=94), {"cluster": 1, "chunk": 32, "n_vox": 40}),
+]
+
+
+@pytest.mark.parametrize("name,make,opts", D2_CASES, ids=[c[0] for c in D2_CASES])
+def test_distance_state_matches_oracle_bit_for_bit(rf, name, make, opts):
+    """Alg. 1's D after M samples: every point's stored FP32 squared distance equals the oracle's,
+    bit for bit (pruned and skipped points included, since pruning and skipping are exact), after
+    rfps_index_sample and again after rfps_index_sample_more."""
+    pts = make().astype(np.float32)
+    n = pts.shape[0]
+    m1, m2 = n // 20, n // 40
+    ix = rf.Index(dev(pts), opts=opts)
+    idx1 = ix.sample(m1, 3).cpu().numpy()
+    d1 = ix.distances().cpu().numpy()
+    ref1, rd1 = oracle.fps(pts, m1, 3, threads=0, return_d2=True)
+    np.testing.assert_array_equal(idx1, ref1)
+    np.testing.assert_array_equal(d1.view(np.uint32), np.asarray(rd1, np.float32).view(np.uint32))
+    idx2 = ix.sample_more(m2).cpu().numpy()
+    d2 = ix.distances().cpu().numpy()
+    ref2, rd2 = oracle.fps(pts, m1 + m2, 3, threads=0, return_d2=True)
+    np.testing.assert_array_equal(idx2, ref2[m1:])
+    np.testing.assert_array_equal(d2.view(np.uint32), np.asarray(rd2, np.float32).view(np.uint32))
+    ix.free()
