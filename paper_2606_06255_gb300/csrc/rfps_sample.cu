@@ -247,7 +247,6 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const uint32_t rank = CLUSTER ? cluster_ctarank() : 0u;
     const uint32_t C = CLUSTER ? cluster_nctarank() : 1u;
-    if (a.hdr->status != 0) return;   // same value in every CTA: uniform exit
     if (t == 0) {
         s_abort = 0;
         if (CLUSTER) {
@@ -276,7 +275,10 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
 
     for (;;) {
         if (rank == 0 && t == 0) {
-            const uint32_t item = atomicAdd(&a.hdr->work, 1u);
+            // an error recorded anywhere in the launch (before it or by another group) ends this
+            // group: one decision, taken by rank 0 and sent to every CTA of the cluster
+            uint32_t item = atomicAdd(&a.hdr->work, 1u);
+            if (*static_cast<volatile uint32_t*>(&a.hdr->status) != 0u) item = 0xffffffffu;
             if (CLUSTER) {
                 for (uint32_t r = 0; r < C; ++r)
                     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(map_shared(&s_item, r)), "r"(item)
@@ -822,8 +824,19 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                 }
             }
         }
-        if (CLUSTER) cluster_sync(); else __syncthreads();
-        if (CLUSTER && s_abort) break;   // every CTA of an aborted cluster times out in turn
+        if (CLUSTER) {
+            // leave together: a CTA that gave up on a wait ends the loop for the whole cluster (one
+            // that left alone would strand the others at the next cluster barrier).  Thread r reads
+            // rank r's flag; the second barrier keeps every CTA alive until all have read.
+            cluster_sync();
+            uint32_t ab = 0;
+            if (t < static_cast<int>(C)) ab = ld_cluster_u32(map_shared(&s_abort, static_cast<uint32_t>(t)));
+            ab = __syncthreads_or(ab);
+            cluster_sync();
+            if (ab) break;
+        } else {
+            __syncthreads();
+        }
     }
     if (COUNTERS) {
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[0]), cn.tests);
