@@ -2,8 +2,9 @@
 
 Sizes are those of the benchmark configurations: the room-like cloud
 (N = 100,000, M = 25,000), the accumulated LiDAR scan (N = 1,124,730,
-M = 16,384), and the ragged 64-cloud batch (M = N/4 each), all through the
-default launch configuration that bench.py times.
+M = 16,384), and the ragged 64-cloud batch (M = N/4 each), through the
+library defaults and through every launch shape the benchmark's autotuner
+can pick (so the timed configuration is always one checked here).
 """
 
 import numpy as np
@@ -22,6 +23,11 @@ def rf():
     return rf
 
 
+# launch shapes the single-cloud benchmark's autotuner chooses between (bench.py TUNE_CANDIDATES)
+BENCH_SHAPES = [{"cluster": 16, "threads": 256}, {"cluster": 16, "threads": 128}, {"cluster": 8, "threads": 256},
+                {"cluster": 16, "threads": 256, "chunk": 256}]
+
+
 @pytest.mark.parametrize("name", ["room100k", "lidar1m"])
 def test_single_cloud_full_size(rf, name):
     (cloud,), _ = cloudgen.workload(name)
@@ -29,6 +35,9 @@ def test_single_cloud_full_size(rf, name):
     d = torch.from_numpy(cloud.points).cuda()
     got = rf.fps(d, cloud.m, cloud.start, check=True).cpu().numpy()
     np.testing.assert_array_equal(got, ref)
+    for o in BENCH_SHAPES:
+        got = rf.fps(d, cloud.m, cloud.start, opts=o, check=True).cpu().numpy()
+        np.testing.assert_array_equal(got, ref, err_msg=str(o))
     # the best plain baseline on the same cloud
     variant = 2 if cloud.points.shape[0] > 200000 else 1
     plain = rf.plain_fps(d, cloud.m, cloud.start, variant=variant).cpu().numpy()
@@ -40,8 +49,10 @@ def test_batch64_full_size(rf):
     sizes = [c.points.shape[0] for c in clouds]
     ms = [c.m for c in clouds]
     cat = torch.from_numpy(np.concatenate([c.points for c in clouds])).cuda()
-    out, ooff = rf.fps_batched(cat, sizes, ms, [0] * len(clouds))
-    out = out.cpu().numpy()
-    for b, c in enumerate(clouds):
-        ref = oracle.fps(c.points, c.m, 0, threads=0)
-        np.testing.assert_array_equal(out[ooff[b]:ooff[b + 1]], ref, err_msg=f"cloud {b} (N={sizes[b]})")
+    refs = [oracle.fps(c.points, c.m, 0, threads=0) for c in clouds]
+    # library defaults and the batch autotuner's pick on this batch (clusters of 8 x 256 threads)
+    for o in (None, {"cluster": 8, "threads": 256, "chunk": 128}):
+        out, ooff = rf.fps_batched(cat, sizes, ms, [0] * len(clouds), opts=o)
+        out = out.cpu().numpy()
+        for b, c in enumerate(clouds):
+            np.testing.assert_array_equal(out[ooff[b]:ooff[b + 1]], refs[b], err_msg=f"cloud {b} (N={sizes[b]}), {o}")

@@ -206,3 +206,9 @@ def test_two_ranks_over_gloo_shard_without_collectives_on_data():
     assert sorted(merged) == list(range(len(sizes)))
     for b, n in enumerate(sizes):
         assert merged[b] == oracle.fps(cloudgen.uniform_cloud(n, seed=500 + b), ms[b], 0).tolist()
+
+
+def test_full_size_parity_covers_every_shape_the_bench_can_time():
+    import bench
+    import test_gpu_fullsize
+    assert bench.TUNE_CANDIDATES == test_gpu_fullsize.BENCH_SHAPES
