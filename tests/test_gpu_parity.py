@@ -385,3 +385,72 @@ def test_distance_state_matches_oracle_bit_for_bit(rf, name, make, opts):
     np.testing.assert_array_equal(idx2, ref2[m1:])
     np.testing.assert_array_equal(d2.view(np.uint32), np.asarray(rd2, np.float32).view(np.uint32))
     ix.free()
+
+
+def _fuzz_cloud(rng, kind, n):
+    if kind == "uniform":
+        return cloudgen.uniform_cloud(n, seed=int(rng.integers(1 << 30)))
+    if kind == "room":
+        return cloudgen.room_cloud(n, seed=int(rng.integers(1 << 30)))
+    if kind == "lidar":   # random subsets of one scan (generating a scan per seed is slow)
+        return cloudgen.lidar_cloud(n, seed=int(rng.integers(1 << 30)), scan_seed=0)
+    if kind == "lattice":
+        side = max(1, int(round(n ** (1 / 3))))
+        g = _lattice(side, side, max(1, n // (side * side)))
+        return g[:n] if g.shape[0] >= n else np.concatenate([g, g[: n - g.shape[0]]])
+    if kind == "duplicates":
+        base = cloudgen.uniform_cloud(max(1, n // 7), seed=int(rng.integers(1 << 30)))
+        return base[rng.integers(0, base.shape[0], n)]
+    flat = cloudgen.uniform_cloud(n, seed=int(rng.integers(1 << 30)))
+    flat[:, int(rng.integers(3))] = np.float32(rng.uniform(-5, 5))
+    return flat
+
+
+def _fuzz_opts(rng):
+    o = {"cluster": int(rng.choice([1, 2, 4, 8, 16])), "threads": int(rng.choice([128, 256, 512])),
+         "chunk": int(rng.choice([32, 64, 128, 256, 1024, 4096]))}
+    if rng.random() < 0.5:
+        o["n_vox"] = int(rng.integers(1, 97))
+    if rng.random() < 0.2:
+        o["prune"] = 0
+    if rng.random() < 0.2:
+        o["skip"] = 0
+    if rng.random() < 0.2:
+        o["radius_mode"] = 1
+    return o
+
+
+KINDS = ["uniform", "room", "lidar", "lattice", "duplicates", "flat"]
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_fuzz_single_cloud(rf, seed):
+    """Seeded random cloud kind, size, M, start and option set: indices equal the oracle's."""
+    rng = np.random.default_rng(1000 + seed)
+    kind = KINDS[seed % len(KINDS)]
+    n = int(np.exp(rng.uniform(0, np.log(40000))))
+    pts = _fuzz_cloud(rng, kind, n).astype(np.float32)
+    n = pts.shape[0]
+    m = int(rng.integers(1, min(n, 3000) + 1))
+    start = int(rng.integers(0, n))
+    o = _fuzz_opts(rng)
+    np.testing.assert_array_equal(gpu_fps(rf, pts, m, start, **o), oracle.fps(pts, m, start, threads=0),
+                                  err_msg=f"{kind} n={n} m={m} start={start} {o}")
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_fuzz_batched(rf, seed):
+    """Seeded random ragged batches (kinds, sizes, M, starts) under a random option set."""
+    rng = np.random.default_rng(2000 + seed)
+    b = int(rng.integers(1, 12))
+    clouds = [_fuzz_cloud(rng, KINDS[int(rng.integers(len(KINDS)))], int(np.exp(rng.uniform(0, np.log(20000)))))
+              .astype(np.float32) for _ in range(b)]
+    sizes = [c.shape[0] for c in clouds]
+    ms = [int(rng.integers(1, min(n, 1500) + 1)) for n in sizes]
+    starts = [int(rng.integers(0, n)) for n in sizes]
+    o = _fuzz_opts(rng)
+    out, ooff = rf.fps_batched(dev(np.concatenate(clouds)), sizes, ms, starts, opts=o)
+    out = out.cpu().numpy()
+    for i, c in enumerate(clouds):
+        np.testing.assert_array_equal(out[ooff[i]:ooff[i + 1]], oracle.fps(c, ms[i], starts[i], threads=0),
+                                      err_msg=f"cloud {i} n={sizes[i]} {o}")
