@@ -454,3 +454,28 @@ def test_fuzz_batched(rf, seed):
     for i, c in enumerate(clouds):
         np.testing.assert_array_equal(out[ooff[i]:ooff[i + 1]], oracle.fps(c, ms[i], starts[i], threads=0),
                                       err_msg=f"cloud {i} n={sizes[i]} {o}")
+
+
+def test_batched_rejects_bad_device_metadata(rf):
+    """Per-cloud arrays are checked on the device (Alg. 2 preprocessing takes them as given): a
+    sample count above the cloud size, a start outside it, or offsets that do not cover the points
+    end the call with RFPS_EINVAL in the status word, and the workspace then serves a valid batch."""
+    sizes = [500, 800, 300]
+    clouds = [cloudgen.uniform_cloud(n, seed=40 + i) for i, n in enumerate(sizes)]
+    cat = dev(np.concatenate(clouds))
+    ws = torch.empty(rf.batch_workspace_size(cat.shape[0], 3, max(sizes)), dtype=torch.uint8, device="cuda")
+    for ms, starts in (([10, 900, 5], [0, 0, 0]), ([10, 20, 5], [0, 800, 0]), ([10, 20, 5], [0, -1, 0])):
+        meta = rf._lib._batch_meta(sizes, ms, starts, cat.device)
+        rf.fps_batched(cat, sizes, ms, starts, workspace=ws, meta=meta)
+        assert rf.status(ws) == 1, (ms, starts)
+    d_off, d_ooff, d_st, off, ooff, max_n = rf._lib._batch_meta(sizes, [10, 20, 5], [0, 0, 0], cat.device)
+    short = d_off.clone()
+    short[-1] = short[-1] - 1                      # offsets end before the last point
+    rf.fps_batched(cat, sizes, [10, 20, 5], [0, 0, 0], workspace=ws, meta=(short, d_ooff, d_st, off, ooff, max_n))
+    assert rf.status(ws) == 1
+    ms = [100, 200, 50]
+    out, oo = rf.fps_batched(cat, sizes, ms, [0, 0, 0], workspace=ws)
+    assert rf.status(ws) == 0
+    out = out.cpu().numpy()
+    for b, c in enumerate(clouds):
+        np.testing.assert_array_equal(out[oo[b]:oo[b + 1]], oracle.fps(c, ms[b], 0))
