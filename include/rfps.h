@@ -54,7 +54,8 @@ typedef enum {
     RFPS_ENOMEM = 3,      /* workspace too small, or a device allocation failed */
     RFPS_ECUDA = 4,       /* a CUDA runtime call failed */
     RFPS_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
-    RFPS_EUNSUPPORTED = 6 /* no sm_103a device, or a launch shape the device cannot run */
+    RFPS_EUNSUPPORTED = 6, /* no sm_103a device, or a launch shape the device cannot run */
+    RFPS_EBOUNDS = 7      /* bounds-checked test builds only: an index taken from data was out of range */
 } rfps_status;
 
 /* Tuning knobs.  Zero means "choose automatically" for every field but the

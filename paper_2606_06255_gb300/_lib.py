@@ -15,7 +15,8 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "librfps.so")
+# RFPS_LIBRARY selects another build of the same library (the bounds-checked test build)
+LIB_PATH = os.environ.get("RFPS_LIBRARY") or os.path.join(_HERE, "librfps.so")
 
 OK, EINVAL, ENONFINITE, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(7)
 

@@ -31,9 +31,11 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def flags(verbose: bool = False) -> list[str]:
+def flags(verbose: bool = False, checked: bool = False) -> list[str]:
     f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC,-O2",
                 "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]
+    if checked:
+        f += ["-DRFPS_CHECKED"]
     if verbose:
         f += ["-Xptxas", "-v"]
     return f
@@ -46,8 +48,12 @@ def _stale(out: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, checked: bool = False) -> str:
+    """Compile and link the library; checked=True builds the bounds-checked test variant
+    (librfps_checked.so, -DRFPS_CHECKED) beside it."""
+    build_dir = BUILD + ("-checked" if checked else "")
+    lib = os.path.join(HERE, "librfps_checked.so") if checked else LIB
+    os.makedirs(build_dir, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "rfps.h"))
     cc = nvcc()
@@ -55,10 +61,10 @@ def build(verbose: bool = False, force: bool = False) -> str:
     jobs = []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(BUILD, s.replace(".cu", ".o"))
+        obj = os.path.join(build_dir, s.replace(".cu", ".o"))
         objs.append(obj)
         if force or verbose or _stale(obj, [src] + headers):
-            jobs.append([cc, *flags(verbose), "-c", src, "-o", obj])
+            jobs.append([cc, *flags(verbose, checked), "-c", src, "-o", obj])
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         results = list(ex.map(lambda cmd: subprocess.run(cmd, capture_output=True, text=True), jobs))
     for cmd, r in zip(jobs, results):
@@ -66,18 +72,18 @@ def build(verbose: bool = False, force: bool = False) -> str:
             sys.stderr.write(r.stderr)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
-    stamp = LIB + ".arch"
+    stamp = lib + ".arch"
     if not os.path.exists(stamp) or open(stamp).read().strip() != platform.machine():
         force = True
-    if force or _stale(LIB, objs):
-        cmd = [cc, *ARCH, "-shared", "-o", LIB, *objs]
+    if force or _stale(lib, objs):
+        cmd = [cc, *ARCH, "-shared", "-o", lib, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
         with open(stamp, "w") as fh:
             fh.write(platform.machine())
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv))
+    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv, checked="--checked" in sys.argv))

@@ -206,6 +206,7 @@ const char* rfps_status_str(int s)
     case RFPS_ECUDA: return "CUDA runtime error";
     case RFPS_ETIMEOUT: return "device-side wait timed out";
     case RFPS_EUNSUPPORTED: return "unsupported device or launch shape";
+    case RFPS_EBOUNDS: return "index out of range (bounds-checked build)";
     default: return "unknown status";
     }
 }

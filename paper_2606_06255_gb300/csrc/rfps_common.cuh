@@ -19,6 +19,7 @@ constexpr uint32_t kStatusInval = 1;
 constexpr uint32_t kStatusNonFinite = 2;
 constexpr uint32_t kStatusTimeout = 5;
 constexpr uint32_t kStatusUnsupported = 6;
+constexpr uint32_t kStatusBounds = 7;      // bounds-checked builds only
 
 // Canonical FP32 squared distance between p and s.
 __device__ __forceinline__ float sq_dist(float px, float py, float pz, float sx, float sy, float sz)

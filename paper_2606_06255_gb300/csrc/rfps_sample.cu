@@ -56,9 +56,27 @@ struct SampleArgs {
     int prune, skip;
     int resident;              // 1: keep records' points in shared memory while they fit
     int save_state;            // 1: write the sampling state back at the end (resumable index)
+#ifdef RFPS_CHECKED
+    uint32_t n_total;          // points of all clouds (the length of pts4 / porig)
+#endif
 };
 
 constexpr int kMaxCluster = 16;
+
+// Bounds-checked test builds (-DRFPS_CHECKED): an index taken from data (a record's range, a list
+// entry, the record that owns a candidate) that falls outside its array records RFPS_EBOUNDS in the
+// status word and the access is skipped.  Every checked index is warp-uniform, so a failed check
+// leaves warp-collective code converged.  Release builds compile the checks away.
+#ifdef RFPS_CHECKED
+#define RFPS_IN(cond) in_bounds((cond), a.hdr)
+__device__ __forceinline__ bool in_bounds(bool ok, WsHeader* hdr)
+{
+    if (!ok) atomicCAS(&hdr->status, 0u, kStatusBounds);
+    return ok;
+}
+#else
+#define RFPS_IN(cond) true
+#endif
 constexpr uint32_t kResident = 0x80000000u;   // rng.x flag: the record's points are in shared memory
 constexpr uint32_t kSpinLimit = 1u << 22;   // try_wait rounds before a wait gives up
 
@@ -308,6 +326,9 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
             uint32_t* s_orig = nullptr;
             uint32_t* s_soff = nullptr;
             bool resident = false;
+#ifdef RFPS_CHECKED
+            uint32_t pcap = 0;   // points the CTA's shared memory holds (fast path)
+#endif
             // hierarchical path (records in global memory, super-records in shared memory)
             float4* s_sct = nullptr;             // super centre, prune threshold
             float4* s_sxyz = nullptr;            // best point of the super, radius in .w
@@ -324,6 +345,9 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                 const size_t poff = (static_cast<size_t>(nloc) * 52 + 15) & ~static_cast<size_t>(15);
                 s_pts = reinterpret_cast<float4*>(smem + poff);
                 const uint32_t P = static_cast<uint32_t>((a.smem_bytes - poff) / 20);
+#ifdef RFPS_CHECKED
+                pcap = P;
+#endif
                 s_orig = reinterpret_cast<uint32_t*>(s_pts + P);
                 uint32_t mine = 0;
                 for (uint32_t l = t; l < nloc; l += NT) {
@@ -555,9 +579,15 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             const uint32_t mm = __shfl_sync(0xffffffffu, rem, src);
                             const uint32_t l = static_cast<uint32_t>(__ffs(mm) - 1) * NT + static_cast<uint32_t>(src * NW + w);
                             if (lane == src) rem &= rem - 1u;
+                            if (!RFPS_IN(l < nloc)) continue;
                             const uint2 rg = v.rng[l];
                             float bx = 0.f, by = 0.f, bz = 0.f;
                             const bool in_smem = resident && (rg.x & kResident);
+#ifdef RFPS_CHECKED
+                            if (!RFPS_IN(in_smem ? (rg.x & ~kResident) + rg.y <= pcap
+                                                 : static_cast<uint64_t>(rg.x) + rg.y <= a.n_total))
+                                continue;
+#endif
                             const unsigned long long lk =
                                 !in_smem ? visit_points<PPL, COUNTERS>(a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx,
                                                                        sy, sz, lane, bx, by, bz, cn)
@@ -585,8 +615,12 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         // one warp updates record l (global memory) and refreshes its key, best point
                         // and prune threshold
                         auto visit_global = [&](uint32_t l) {
+                            if (!RFPS_IN(l < nloc)) return;
                             const uint32_t k = v.g(l);
                             const uint2 rg = a.rec_rng[k];
+#ifdef RFPS_CHECKED
+                            if (!RFPS_IN(static_cast<uint64_t>(rg.x) + rg.y <= a.n_total)) return;
+#endif
                             float bx = 0.f, by = 0.f, bz = 0.f;
                             const unsigned long long lk = visit_points<PPL, COUNTERS>(
                                 a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx, sy, sz, lane, bx, by, bz, cn);
@@ -650,6 +684,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         // go to the record list, or are visited in place when the list is full
                         for (uint32_t i = w; i < nsl; i += NW) {
                             const uint32_t g = s_slist[i];
+                            if (!RFPS_IN(g < G)) continue;
                             const uint32_t l = g * 32 + lane;
                             bool keep = false;
                             if (l < nloc) {
@@ -694,6 +729,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         // ---- C: refresh the unpruned super-records from their records
                         for (uint32_t i = w; i < nsl; i += NW) {
                             const uint32_t g = s_slist[i];
+                            if (!RFPS_IN(g < G)) continue;
                             const uint32_t l = g * 32 + lane;
                             unsigned long long kk = 0ull;
                             float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -741,7 +777,8 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         // may rewrite its best point in the next iteration, before a slower warp reads it)
                         if (lane == 0) {
                             s_wkey[par][w] = wk;
-                            s_wxyz[par][w] = wk != 0ull ? (FAST ? v.best[wr] : s_sxyz[wr]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            s_wxyz[par][w] = wk != 0ull && RFPS_IN(wr < (FAST ? nloc : G))
+                                                 ? (FAST ? v.best[wr] : s_sxyz[wr]) : make_float4(0.f, 0.f, 0.f, 0.f);
                         }
                         __syncthreads();
                         const unsigned long long ck = lane < NW ? s_wkey[par][lane] : 0ull;
@@ -757,7 +794,8 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         const uint32_t nslot = C * NW;
                         if (t == 0) mbar_arrive_expect_tx(&s_mbar[buf], 24u * nslot);
                         float4 wxyz = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (wk != 0ull && lane < static_cast<int>(C)) wxyz = FAST ? v.best[wr] : s_sxyz[wr];
+                        if (wk != 0ull && lane < static_cast<int>(C) && RFPS_IN(wr < (FAST ? nloc : G)))
+                            wxyz = FAST ? v.best[wr] : s_sxyz[wr];
                         if (lane < static_cast<int>(C)) {
                             const uint32_t rb = buf ? rbar1 : rbar0;
                             st_async_u64(buf ? rkey1 : rkey0, wk, rb);
@@ -1026,6 +1064,9 @@ cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int6
     a.smem_bytes = 0;   // set per instantiation from the device's opt-in limit
     a.resident = 1;
     a.save_state = save_state ? 1 : 0;
+#ifdef RFPS_CHECKED
+    a.n_total = static_cast<uint32_t>(L.total_n);
+#endif
     const int C = o.cluster;
     const bool cl = C > 1;
     if (o.counters) {

@@ -33,7 +33,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_status_strings(lib):
-    for code in range(7):
+    for code in range(8):
         s = lib.rfps_status_str(code)
         assert s and s != b"unknown status"
     assert lib.rfps_status_str(99) == b"unknown status"

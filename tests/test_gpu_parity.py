@@ -479,3 +479,28 @@ def test_batched_rejects_bad_device_metadata(rf):
     out = out.cpu().numpy()
     for b, c in enumerate(clouds):
         np.testing.assert_array_equal(out[oo[b]:oo[b + 1]], oracle.fps(c, ms[b], 0))
+
+
+@pytest.mark.parametrize("name,make,opts", [
+    ("uniform_7_c1", lambda: cloudgen.uniform_cloud(7, seed=3), {"cluster": 1}),
+    ("uniform_64_c16", lambda: cloudgen.uniform_cloud(64, seed=4), {"cluster": 16, "threads": 128}),
+    ("room_64_c4", lambda: cloudgen.room_cloud(64, seed=5), {"cluster": 4}),
+    ("lattice_ties_c2", lambda: _lattice(4, 4, 4), {"cluster": 2, "chunk": 32, "n_vox": 3}),
+    ("duplicates_c8", lambda: cloudgen.uniform_cloud(9, seed=6)[np.arange(48) % 9], {"cluster": 8}),
+])
+def test_distance_state_every_iteration_small(rf, name, make, opts):
+    """Small clouds stepped one sample at a time (rfps_index_sample_more(1)): after every iteration the
+    whole distance array D equals the oracle's bit for bit, and so does the new index."""
+    pts = make().astype(np.float32)
+    n = pts.shape[0]
+    start = n // 3
+    ix = rf.Index(dev(pts), opts=opts)
+    got = list(ix.sample(2, start).cpu().numpy())
+    for m in range(2, n + 1):
+        if m > 2:
+            got.append(int(ix.sample_more(1).cpu().numpy()[0]))
+        ref, rd = oracle.fps(pts, m, start, threads=0, return_d2=True)
+        np.testing.assert_array_equal(np.array(got), ref, err_msg=f"m={m}")
+        d = ix.distances().cpu().numpy()
+        np.testing.assert_array_equal(d.view(np.uint32), np.asarray(rd, np.float32).view(np.uint32), err_msg=f"m={m}")
+    ix.free()
