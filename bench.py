@@ -279,10 +279,17 @@ def run_study(args, rf, torch, cloud, pts, opts):
     return 0
 
 
-def run_batch64(args, rf, torch):
-    """64 ragged clouds: one graph-replayed batched launch vs 64 per-cloud launches vs plain batched."""
+def run_batch64(args, rf, torch, world=1, rank=0):
+    """64 ragged clouds: one graph-replayed batched launch vs 64 per-cloud launches vs plain batched.
+
+    Under torchrun the clouds are sharded over the ranks (largest work first, no data-path
+    collective); each rank samples its share as one batch, and the batch time is the slowest
+    rank's (strong scaling: the 64 clouds are the whole job)."""
     import cloudgen
-    clouds, desc = cloudgen.workload("batch64")
+    from paper_2606_06255_gb300 import shard
+    all_clouds, desc = cloudgen.workload("batch64")
+    mine = shard.my_clouds([c.points.shape[0] for c in all_clouds], [c.m for c in all_clouds], world, rank)
+    clouds = [all_clouds[b] for b in mine]
     sizes = [c.points.shape[0] for c in clouds]
     ms = [c.m for c in clouds]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -301,8 +308,23 @@ def run_batch64(args, rf, torch):
     for _ in range(max(args.warmup, 3)):
         bs.run()
     torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
     t_batch = _events(torch, bs.run, args.steps, flush)
     launches = bs.kernels_per_run
+    if world > 1:
+        t = torch.tensor([t_batch], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_batch = float(t.item())
+        if rank == 0:
+            print(json.dumps({
+                "metric": "clouds/s", "value": len(all_clouds) / (t_batch / 1e3), "unit": "clouds/s",
+                "workload": "batch64", "desc": desc, "n_gpus": world, "scaling": "strong",
+                "clouds": len(all_clouds), "clouds_rank0": len(clouds), "ms_per_batch": t_batch,
+                "samples_per_s": sum(c.m for c in all_clouds) / (t_batch / 1e3), "opts_rank0": opts,
+                "graph": True, "gpu_launches_per_batch_rank0": launches}), flush=True)
+        return 0
     ref = bs.out.cpu().numpy()
     cat, off = bs.points, bs.offsets
     views = [cat[int(off[b]):int(off[b + 1])] for b in range(len(sizes))]
@@ -333,18 +355,33 @@ def run_batch64(args, rf, torch):
     return 0
 
 
-def run_serving(args, rf):
-    """Poisson request stream through the continuous-batching server."""
+def run_serving(args, rf, world=1, rank=0):
+    """Poisson request stream through the continuous-batching server.  Under torchrun the stream
+    is sharded round-robin over the ranks, each serving its share on its own GPU; rank 0 merges
+    the outcomes (latency percentiles and throughput over the whole stream)."""
     from paper_2606_06255_gb300 import serve
     # throughput setting: one CTA of 512 threads per cloud (the most SM-efficient shape), many streams
     opts = json.loads(args.opts) if args.opts else {"cluster": 1, "threads": 512}
     reqs = serve.poisson_workload(args.requests + 16, args.rate, pinned=True)
     ex = serve.GpuExecutor(args.slots, opts=opts)
     srv = serve.Server(ex, mem_budget=48 << 30, max_inflight=args.slots, max_batch=args.max_batch)
-    srv.run(reqs[:16])
+    srv.run([r for r in reqs[:16] if r.rid % world == rank])
     t0 = reqs[16].arrival
-    rep = srv.run([serve.Request(r.rid, r.arrival - t0, r.points, r.m, r.start) for r in reqs[16:]])
+    timed = [serve.Request(r.rid, r.arrival - t0, r.points, r.m, r.start) for r in reqs[16:] if r.rid % world == rank]
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    rep = srv.run(timed)
+    if world > 1:
+        for c in rep.completed:   # the indices stay on their rank; only the outcome travels
+            c.indices = None
+        parts = [None] * world
+        dist.all_gather_object(parts, rep)
+        if rank != 0:
+            return 0
+        rep = serve.merge_reports(parts)
     out = rep.summary()
+    out["n_gpus"] = world
     out.update({"metric": "p99 latency / clouds/s", "workload": "serving", "offered_rate": args.rate,
                 "requests": args.requests, "opts": opts, "slots": args.slots, "max_batch": args.max_batch,
                 "sizes": "N log-uniform [20000, 1200000], M = N/8, half room / half LiDAR"})
@@ -372,12 +409,18 @@ def main():
                 print(json.dumps({"cluster": cluster, "threads": threads, "ns_per_iteration": ms * 1e6 / 24999}),
                       flush=True)
         return 0
-    if args.workload == "batch64":
-        return run_batch64(args, rf, torch)
-    if args.workload == "serving":
-        return run_serving(args, rf)
-    if world > 1:
+    if world > 1 and not args.floor_sweep:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "batch64":
+        rc = run_batch64(args, rf, torch, world, rank)
+    elif args.workload == "serving":
+        rc = run_serving(args, rf, world, rank)
+    else:
+        rc = None
+    if rc is not None:
+        if world > 1:
+            dist.destroy_process_group()
+        return rc
     dev = torch.device("cuda", local)
     (cloud,), desc = cloudgen.workload(args.workload, seed=rank)
     n, m, start = cloud.points.shape[0], cloud.m, cloud.start

@@ -55,6 +55,7 @@ class Completed:
     finished: float
     batch_size: int
     indices: np.ndarray
+    samples: int = 0        # len(indices), kept when the indices themselves are dropped
 
     @property
     def latency(self) -> float:
@@ -98,8 +99,32 @@ class Report:
             "mean_batch_size": statistics.mean(c.batch_size for c in self.completed) if n else None,
             "max_inflight_batches": self.max_inflight_batches,
             "peak_device_bytes": self.peak_mem,
-            "samples_per_s": sum(len(c.indices) for c in self.completed) / self.makespan if self.makespan else None,
+            "samples_per_s": sum(c.samples for c in self.completed) / self.makespan if self.makespan else None,
         }
+
+
+def merge_reports(reports) -> "Report":
+    """One report for a request stream served by several servers (one per GPU, each with a share of
+    the requests): outcomes concatenated; the arrival window, offered rate and makespan taken over
+    the whole stream; peak device memory summed over the servers."""
+    out = Report()
+    live = [r for r in reports if r.window != (0.0, 0.0) or r.completed]
+    for r in reports:
+        out.completed += r.completed
+        out.rejected += r.rejected
+        out.failed += r.failed
+        out.expired += r.expired
+        out.cancelled += r.cancelled
+        out.max_inflight_batches = max(out.max_inflight_batches, r.max_inflight_batches)
+        out.peak_mem += r.peak_mem
+    if live:
+        t0 = min(r.window[0] for r in live)
+        t1 = max(r.window[1] for r in live)
+        out.window = (t0, t1)
+        n = len(out.completed) + len(out.rejected) + len(out.failed) + len(out.expired) + len(out.cancelled)
+        out.offered_rate = (n - 1) / (t1 - t0) if t1 > t0 else float("inf")
+        out.makespan = max(r.window[0] + r.makespan for r in live) - t0
+    return out
 
 
 class Server:
@@ -173,7 +198,7 @@ class Server:
                         requeue(batch, f"results: {e}")
                     if results is not None:
                         for r, idx in zip(batch, results):
-                            rep.completed.append(Completed(r.rid, r.arrival, t_adm, t_done, len(batch), idx))
+                            rep.completed.append(Completed(r.rid, r.arrival, t_adm, t_done, len(batch), idx, len(idx)))
                         last_finish = max(last_finish, t_done)
                     mem_used -= mem
                     free_slots.append(slot)
@@ -286,18 +311,22 @@ class GpuExecutor:
                 ws.data_ptr(), ws.numel(), s.cuda_stream), "rfps_fps_batched")
             host_out = torch.empty(mtotal, dtype=torch.int64, pin_memory=True)
             host_out.copy_(out, non_blocking=True)
+            # the workspace's status word (its first 4 bytes) comes back with the indices, so that
+            # results() reads it without a synchronising call
+            host_st = torch.empty(1, dtype=torch.int32, pin_memory=True)
+            host_st.copy_(ws[:4].view(torch.int32), non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(s)
         ooff = np.concatenate([[0], np.cumsum(ms)])
         # keep every buffer alive until the event completes
-        return {"event": ev, "host_out": host_out, "ooff": ooff, "ws": ws, "stream": s,
+        return {"event": ev, "host_out": host_out, "host_st": host_st, "ooff": ooff,
                 "keep": (meta, dmeta, pts, ws, out, staged)}
 
     def done(self, handle) -> bool:
         return handle["event"].query()
 
     def results(self, handle):
-        st = self.lib.status(handle["ws"], handle["stream"])   # the launch has completed: no wait
+        st = int(handle["host_st"][0])   # copied back with the indices; the event has fired
         if st != 0:
             raise RuntimeError(f"device status {st}")
         o, ooff = handle["host_out"].numpy(), handle["ooff"]

@@ -212,3 +212,26 @@ def test_full_size_parity_covers_every_shape_the_bench_can_time():
     import bench
     import test_gpu_fullsize
     assert bench.TUNE_CANDIDATES == test_gpu_fullsize.BENCH_SHAPES
+
+
+def test_reports_of_sharded_servers_merge_into_the_whole_stream():
+    """Two servers (one per GPU) each serve half of a request stream; the merged report has every
+    outcome once, the window and offered rate of the whole stream, and the same latencies."""
+    reqs = _requests(40, rate=3000.0, seed=21)
+    whole_window = (reqs[0].arrival, reqs[-1].arrival)
+    parts = []
+    for rank in range(2):
+        clk = FakeClock()
+        ex = SimExecutor(clk)
+        mine = [r for r in reqs if r.rid % 2 == rank]
+        parts.append(serve.Server(ex, mem_budget=10**9, max_inflight=3, max_batch=4).run(mine, clock=clk,
+                                                                                      sleep=clk.sleep))
+    merged = serve.merge_reports(parts)
+    assert sorted(c.rid for c in merged.completed) == [r.rid for r in reqs]
+    assert merged.window == whole_window
+    assert abs(merged.offered_rate - (len(reqs) - 1) / (whole_window[1] - whole_window[0])) < 1e-9
+    lat = sorted(c.latency for p in parts for c in p.completed)
+    assert sorted(c.latency for c in merged.completed) == lat
+    s = merged.summary()
+    assert s["requests_completed"] == 40 and s["p99_latency_ms"] >= s["p50_latency_ms"] > 0
+    assert s["samples_per_s"] > 0
