@@ -518,6 +518,25 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     unsigned long long pk;   // this lane's partial max (key, record) for the selection
                     uint32_t prec;
                     uint32_t vis = 0;        // my records visited now (bit b: record b * NT + my)
+                    // a visited record's bookkeeping waits until the warp's candidate is pushed
+                    uint32_t dl = 0xffffffffu;
+                    unsigned long long dk = 0ull;
+                    float dx = 0.f, dy = 0.f, dz = 0.f;
+                    bool ppt = false;        // this lane's candidate is a point of a record visited now
+                    float px = 0.f, py = 0.f, pz = 0.f;
+                    auto finish_record = [&](uint32_t l, unsigned long long lk, float bx, float by, float bz) {
+                        unsigned long long rk;
+                        const int rl = warp_argmax_lane(lk, &rk);
+                        const float wx = __shfl_sync(0xffffffffu, bx, rl);
+                        const float wy = __shfl_sync(0xffffffffu, by, rl);
+                        const float wz = __shfl_sync(0xffffffffu, bz, rl);
+                        if (lane == 0) {
+                            const float r = v.best[l].w;
+                            v.key[l] = rk;
+                            v.best[l] = make_float4(wx, wy, wz, r);
+                            v.ct[l].w = prune_threshold(r, rk);
+                        }
+                    };
                     if constexpr (FAST) {
                         // ---- prune test of my records (bit b of um: record b * NT + my is kept)
                         uint32_t um = 0;
@@ -595,19 +614,40 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                                                                           first, a.skip, sx, sy, sz, lane, bx, by, bz, cn)
                                             : visit_points<PPL, COUNTERS>(s_pts, s_orig, rg.x & ~kResident, rg.y, first,
                                                                           a.skip, sx, sy, sz, lane, bx, by, bz, cn);
-                            unsigned long long rk;
-                            const int wl = warp_argmax_lane(lk, &rk);
-                            const float wx = __shfl_sync(0xffffffffu, bx, wl);
-                            const float wy = __shfl_sync(0xffffffffu, by, wl);
-                            const float wz = __shfl_sync(0xffffffffu, bz, wl);
-                            if (lane == 0) {
-                                const float r = v.best[l].w;
-                                v.key[l] = rk;
-                                v.best[l] = make_float4(wx, wy, wz, r);
-                                v.ct[l].w = prune_threshold(r, rk);
-                                if (rk > pk) {
-                                    pk = rk;
-                                    prec = l;
+                            if constexpr (CLUSTER) {
+                                // the candidate may now be a visited point (its coordinates are in
+                                // registers); the record's own update waits until the candidate is
+                                // pushed, overlapping the exchange (one record pending at most)
+                                if (lk > pk) {
+                                    pk = lk;
+                                    ppt = true;
+                                    px = bx;
+                                    py = by;
+                                    pz = bz;
+                                }
+                                if (dl != 0xffffffffu) finish_record(dl, dk, dx, dy, dz);
+                                dl = l;
+                                dk = lk;
+                                dx = bx;
+                                dy = by;
+                                dz = bz;
+                            } else {
+                                // one CTA: a CTA barrier follows the selection and nothing would overlap
+                                // the update, so it is done here and merged into lane 0's candidate
+                                unsigned long long rk;
+                                const int rl = warp_argmax_lane(lk, &rk);
+                                const float wx = __shfl_sync(0xffffffffu, bx, rl);
+                                const float wy = __shfl_sync(0xffffffffu, by, rl);
+                                const float wz = __shfl_sync(0xffffffffu, bz, rl);
+                                if (lane == 0) {
+                                    const float r = v.best[l].w;
+                                    v.key[l] = rk;
+                                    v.best[l] = make_float4(wx, wy, wz, r);
+                                    v.ct[l].w = prune_threshold(r, rk);
+                                    if (rk > pk) {
+                                        pk = rk;
+                                        prec = l;
+                                    }
                                 }
                             }
                         }
@@ -763,13 +803,19 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     }
                     // ---- selection: warp -> CTA -> cluster
                     __syncwarp();
-                    if constexpr (NREG > 0) {   // thresholds rewritten by this iteration's visits
-                        if (vis & 1u) ct0.w = v.ct[my].w;
-                        if (NREG == 2 && (vis & 2u)) ct1.w = v.ct[my + NT].w;
-                    }
                     unsigned long long wk;
                     const int wl = warp_argmax_lane(pk, &wk);
                     const uint32_t wr = __shfl_sync(0xffffffffu, prec, wl);
+                    bool wpt = false;                 // the warp's candidate is a point visited now
+                    float4 vxyz = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if constexpr (FAST && CLUSTER) {
+                        wpt = __shfl_sync(0xffffffffu, ppt, wl);
+                        if (wpt) {
+                            vxyz.x = __shfl_sync(0xffffffffu, px, wl);
+                            vxyz.y = __shfl_sync(0xffffffffu, py, wl);
+                            vxyz.z = __shfl_sync(0xffffffffu, pz, wl);
+                        }
+                    }
                     float4 cxyz = make_float4(0.f, 0.f, 0.f, 0.f);
                     unsigned long long gbest;
                     if (!CLUSTER) {
@@ -779,6 +825,10 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             s_wkey[par][w] = wk;
                             s_wxyz[par][w] = wk != 0ull && RFPS_IN(wr < (FAST ? nloc : G))
                                                  ? (FAST ? v.best[wr] : s_sxyz[wr]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                        if constexpr (NREG > 0) {   // thresholds rewritten by this iteration's visits
+                            if (vis & 1u) ct0.w = v.ct[my].w;
+                            if (NREG == 2 && (vis & 2u)) ct1.w = v.ct[my + NT].w;
                         }
                         __syncthreads();
                         const unsigned long long ck = lane < NW ? s_wkey[par][lane] : 0ull;
@@ -794,12 +844,21 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         const uint32_t nslot = C * NW;
                         if (t == 0) mbar_arrive_expect_tx(&s_mbar[buf], 24u * nslot);
                         float4 wxyz = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (wk != 0ull && lane < static_cast<int>(C) && RFPS_IN(wr < (FAST ? nloc : G)))
+                        if (wpt) wxyz = vxyz;
+                        else if (wk != 0ull && lane < static_cast<int>(C) && RFPS_IN(wr < (FAST ? nloc : G)))
                             wxyz = FAST ? v.best[wr] : s_sxyz[wr];
                         if (lane < static_cast<int>(C)) {
                             const uint32_t rb = buf ? rbar1 : rbar0;
                             st_async_u64(buf ? rkey1 : rkey0, wk, rb);
                             st_async_f32x4(buf ? rxyz1 : rxyz0, wxyz, rb);
+                        }
+                        if constexpr (FAST) {   // the last visited record's update overlaps the exchange
+                            if (dl != 0xffffffffu) finish_record(dl, dk, dx, dy, dz);
+                            __syncwarp();
+                            if constexpr (NREG > 0) {   // thresholds rewritten by this iteration's visits
+                                if (vis & 1u) ct0.w = v.ct[my].w;
+                                if (NREG == 2 && (vis & 2u)) ct1.w = v.ct[my + NT].w;
+                            }
                         }
                         if (!__all_sync(0xffffffffu, mbar_wait_bounded(&s_mbar[buf], ph, kSpinLimit))) {
                             if (lane == 0) atomicCAS(&a.hdr->status, 0u, kStatusTimeout);
