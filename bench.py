@@ -82,7 +82,9 @@ def load_peaks():
 
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 50 ms; only readings that arrive inside the
-    timed region (between mark() and stop()) count."""
+    timed region (between mark() and stop()) count.  A timed region shorter than the sampling
+    interval may see none: then the last reading before it and the first one after it are taken,
+    and the result says so ("window": "adjacent")."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -119,6 +121,12 @@ class ClockSampler:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         t1 = time.time()
+        t0 = self.t0 if self.t0 is not None else 0.0
+        adjacent = not any(t0 <= ts <= t1 for ts, _ in self.lines)
+        if adjacent:   # wait for the first reading after the timed region
+            deadline = time.time() + 0.5
+            while not any(ts > t1 for ts, _ in list(self.lines)) and time.time() < deadline:
+                time.sleep(0.01)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -126,8 +134,12 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        t0 = self.t0 if self.t0 is not None else 0.0
-        inside = [ln for ts, ln in self.lines if t0 <= ts <= t1]
+        if adjacent:
+            before = [ln for ts, ln in self.lines if ts < t0][-1:]
+            after = [ln for ts, ln in self.lines if ts > t1][:1]
+            inside = before + after
+        else:
+            inside = [ln for ts, ln in self.lines if t0 <= ts <= t1]
         for ln in inside:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
@@ -142,7 +154,8 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "window": "adjacent" if adjacent else "timed"}
 
 
 # launch shapes the single-cloud benchmark lets the autotuner choose between

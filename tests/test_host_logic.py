@@ -235,3 +235,35 @@ def test_reports_of_sharded_servers_merge_into_the_whole_stream():
     s = merged.summary()
     assert s["requests_completed"] == 40 and s["p99_latency_ms"] >= s["p50_latency_ms"] > 0
     assert s["samples_per_s"] > 0
+
+
+class _FakeSmi:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def _smi_line(mhz, power_cap="Not Active"):
+    return f"0, {mhz}, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, {power_cap}"
+
+
+def test_clock_sampler_counts_only_the_timed_region_and_falls_back_to_adjacent_readings():
+    import time
+    import bench
+    now = time.time()
+    cs = bench.ClockSampler(0)
+    cs.proc = _FakeSmi()
+    cs.t0 = now - 1.0
+    cs.lines = [(now - 2.0, _smi_line(1000)), (now - 0.5, _smi_line(2070)), (now - 0.4, _smi_line(2070, "Active"))]
+    r = cs.stop()
+    assert r["window"] == "timed" and r["samples"] == 2
+    assert r["sm_mhz"] == 2070.0 and r["reasons"] == ["sw_power_cap"]
+    # a timed region with no reading inside: the last one before it and the first one after it
+    cs = bench.ClockSampler(0)
+    cs.proc = _FakeSmi()
+    cs.t0 = now - 0.01
+    cs.lines = [(now - 3.0, _smi_line(500)), (now - 0.05, _smi_line(2060)), (now + 60.0, _smi_line(2070))]
+    r = cs.stop()
+    assert r["window"] == "adjacent" and r["samples"] == 2 and r["sm_mhz"] == 2065.0
