@@ -528,6 +528,12 @@ def main():
 
     # ---- per-iteration synchronisation floor of the launch shape the step used
     rs = rf.resolved_opts(n, opts)
+    # ---- on-chip roofline: after the first touch the loop's bytes come from shared memory and L2,
+    # and one cloud occupies one cluster of SMs
+    smem_bw = rf.bandwidth_probe("smem")
+    l2_bw = rf.bandwidth_probe("l2")
+    sms_used = rs["cluster"]
+    onchip_peak = smem_bw["gbs_per_sm"] * sms_used
     floor_ms = min(rf.sync_floor(rs["cluster"], rs["threads"], max(2, m)) for _ in range(3))
     floor_ns = floor_ms * 1e6 / max(1, m - 1)
 
@@ -551,7 +557,9 @@ def main():
                 p_ms.append(e0.elapsed_time(e1))
             pm = statistics.mean(p_ms)
             plain[label] = {"variant": variant, "ms_per_cloud": pm, "samples_per_s": m / (pm / 1e3),
-                            "radiusfps_speedup": pm / ms_per_step}
+                            "radiusfps_speedup": pm / ms_per_step,
+                            # 16 B (coordinates + d2) per point per iteration, index build included
+                            "achieved_gbs": 16 * n * (m - 1) / (pm / 1e3) / 1e9}
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     host_pts = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
@@ -596,7 +604,12 @@ def main():
                          "peak_kind": peak_kind,
                          "ns_per_iteration": k_ms * 1e6 / max(1, m - 1),
                          "sync_floor_ns_per_iteration": floor_ns,
-                         "launch_shape": {"cluster": rs["cluster"], "threads": rs["threads"]}},
+                         "launch_shape": {"cluster": rs["cluster"], "threads": rs["threads"]},
+                         "onchip": {"bound": "smem", "sms_used": sms_used, "peak": onchip_peak, "unit": "GB/s",
+                                    "frac": achieved / onchip_peak,
+                                    "smem_gbs_per_sm": smem_bw["gbs_per_sm"], "smem_gbs": smem_bw["gbs"],
+                                    "l2_gbs": l2_bw["gbs"], "l2_probe_bytes": l2_bw["buffer_bytes"],
+                                    "peak_kind": "measured by rfps_bandwidth_probe in this run"}},
             "counters": c,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": n * 12,

@@ -232,6 +232,27 @@ rfps_status rfps_sync_floor(int32_t cluster, int32_t threads, int64_t iterations
                             void *workspace, size_t workspace_bytes, void *stream);
 
 /* ------------------------------------------------------------------------
+ * On-chip bandwidth probe, the denominator of the sampling kernel's on-chip
+ * roofline.  After the first touch, the per-iteration traffic of the loop
+ * (record tests, point visits, updates; Sec. 3.3-3.4) is served from shared
+ * memory and L2, not DRAM.  One launch on `stream`, timed by the caller.
+ *   kind 0  L2 reads: every SM streams `bytes` of the device buffer `buf`
+ *           (16-byte aligned, bytes a positive multiple of 16, read only)
+ *           with L2-only loads, `reps` passes.  For the L2 figure the buffer
+ *           must fit in L2 and have been touched once (a warm-up launch).
+ *   kind 1  shared-memory reads: every resident CTA reads a 48 KiB array of
+ *           its own `reps` times, conflict-free; `buf` and `bytes` unused.
+ * reps in [1, 2^20].  `sink`: device, 8-byte aligned, 8 bytes; the probe XORs
+ * what it read into it (its value has no meaning).  On return, the optional
+ * host pointers receive the bytes the launch reads (`bytes_moved`) and the
+ * device's SM count (`sm_count`); read bandwidth = bytes_moved / launch time.
+ * Invalid arguments: RFPS_EINVAL, nothing launched.
+ * ---------------------------------------------------------------------- */
+rfps_status rfps_bandwidth_probe(int32_t kind, const void *buf, int64_t bytes,
+                                 int32_t reps, void *sink, int64_t *bytes_moved,
+                                 int32_t *sm_count, void *stream);
+
+/* ------------------------------------------------------------------------
  * Device status and counters of a workspace.  Both synchronise `stream`.
  * rfps_status_read returns the first error the device recorded for the last
  * call that used `workspace` (RFPS_OK if none).

@@ -12,6 +12,7 @@ from ._lib import (  # noqa: F401
     Opts,
     RfpsError,
     batch_workspace_size,
+    bandwidth_probe,
     counters,
     fps,
     fps_batched,

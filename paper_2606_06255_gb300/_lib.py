@@ -79,6 +79,7 @@ def _load():
         "rfps_plain_workspace_size": (sz, [i64, i64]),
         "rfps_plain_fps": (st, [vp, i64, i64, i64, vp, i32, vp, sz, vp]),
         "rfps_plain_fps_batched": (st, [vp, i64, vp, i64, vp, vp, i64, vp, i32, vp, sz, vp]),
+        "rfps_bandwidth_probe": (st, [i32, vp, i64, i32, vp, ctypes.POINTER(i64), ctypes.POINTER(i32), vp]),
         "rfps_status_read": (st, [vp, vp]),
         "rfps_sync_floor": (st, [i32, i32, i64, vp, sz, vp]),
         "rfps_counters_read": (st, [vp, ctypes.POINTER(Counters), vp]),
@@ -254,6 +255,36 @@ def counters(workspace: torch.Tensor, stream=None) -> dict:
     c = Counters()
     _check(_lib.rfps_counters_read(workspace.data_ptr(), ctypes.byref(c), _stream(stream)), "rfps_counters_read")
     return c.as_dict()
+
+
+def bandwidth_probe(kind: str, nbytes: int = 64 << 20, reps: int | None = None, tries: int = 3,
+                    stream=None) -> dict:
+    """Read bandwidth of L2 ("l2": an `nbytes` buffer, small enough for L2, read with L2-only loads
+    from every SM) or of shared memory ("smem": every resident CTA reads 48 KiB of its own), from
+    the best of `tries` launches timed with CUDA events after a warm-up launch.  GB/s for the whole
+    GPU and per SM."""
+    k = {"l2": 0, "smem": 1}[kind]
+    if reps is None:
+        reps = 100 if k == 0 else 2000
+    st = torch.cuda.current_stream() if stream is None else stream
+    buf = torch.ones(nbytes // 4, dtype=torch.int32, device="cuda") if k == 0 else None
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+    moved, sms = ctypes.c_int64(0), ctypes.c_int32(0)
+    args = (k, buf.data_ptr() if buf is not None else None, nbytes if k == 0 else 0, reps, sink.data_ptr(),
+            ctypes.byref(moved), ctypes.byref(sms), _stream(st))
+    _check(_lib.rfps_bandwidth_probe(*args), "rfps_bandwidth_probe")
+    best = float("inf")
+    for _ in range(tries):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        _check(_lib.rfps_bandwidth_probe(*args), "rfps_bandwidth_probe")
+        e1.record(st)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    gbs = moved.value / (best / 1e3) / 1e9
+    return {"kind": kind, "gbs": gbs, "gbs_per_sm": gbs / max(1, sms.value), "bytes": moved.value, "ms": best,
+            "sms": sms.value, "reps": reps, "buffer_bytes": nbytes if k == 0 else 49152}
 
 
 def sync_floor(cluster: int, threads: int, iterations: int, stream=None) -> float:

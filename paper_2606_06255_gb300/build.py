@@ -20,7 +20,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "librfps.so")
-SOURCES = ["rfps_api.cu", "rfps_build.cu", "rfps_sample.cu", "rfps_plain.cu", "rfps_noalloc.cu"]
+SOURCES = ["rfps_api.cu", "rfps_build.cu", "rfps_sample.cu", "rfps_plain.cu", "rfps_noalloc.cu", "rfps_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

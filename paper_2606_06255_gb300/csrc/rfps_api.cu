@@ -376,6 +376,27 @@ rfps_status rfps_sync_floor(int32_t cluster, int32_t threads, int64_t iterations
                                        static_cast<cudaStream_t>(stream)));
 }
 
+rfps_status rfps_bandwidth_probe(int32_t kind, const void* buf, int64_t bytes, int32_t reps, void* sink,
+                                 int64_t* bytes_moved, int32_t* sm_count, void* stream)
+{
+    if ((kind != 0 && kind != 1) || reps < 1 || reps > (1 << 20) || !sink ||
+        (reinterpret_cast<uintptr_t>(sink) & 7u) != 0)
+        return RFPS_EINVAL;
+    if (kind == 0 && (!buf || (reinterpret_cast<uintptr_t>(buf) & 15u) != 0 || bytes < 16 || bytes % 16 != 0 ||
+                      bytes > (int64_t(1) << 40)))
+        return RFPS_EINVAL;
+    rfps_status s = device_check();
+    if (s != RFPS_OK) return s;
+    int64_t moved = 0;
+    int sms = 0;
+    const cudaError_t e = launch_bw_probe(kind, buf, bytes, reps, static_cast<unsigned long long*>(sink),
+                                          static_cast<cudaStream_t>(stream), &moved, &sms);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (bytes_moved) *bytes_moved = moved;
+    if (sm_count) *sm_count = sms;
+    return RFPS_OK;
+}
+
 rfps_status rfps_status_read(const void* workspace, void* stream)
 {
     if (!workspace) return RFPS_EINVAL;

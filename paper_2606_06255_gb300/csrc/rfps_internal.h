@@ -78,6 +78,9 @@ cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int6
                           bool save_state = false);
 // Synchronisation floor of the sampling loop (same tail, no record work).
 cudaError_t launch_sync_floor(int C, int NT, int64_t iters, unsigned long long* sink, cudaStream_t st);
+// On-chip bandwidth probe (rfps_probe.cu): kind 0 L2 reads of `buf`, kind 1 shared-memory reads.
+cudaError_t launch_bw_probe(int kind, const void* buf, int64_t bytes, int reps, unsigned long long* sink,
+                            cudaStream_t st, int64_t* moved, int* sms_out);
 // Plain FPS launches.
 cudaError_t launch_plain(char* ws, const WsLayout& L, const float* points, int64_t* out, int variant,
                          int64_t n_clouds, int64_t max_n, cudaStream_t st);

@@ -92,6 +92,15 @@ def test_argument_errors_need_no_device(lib):
     assert lib.rfps_fps_batched(fake, 10, None, 1, fake, fake, 10, fake, None, fake, 1 << 20, None) == EINVAL
     assert lib.rfps_index_sample(None, 1, 0, fake, None) == EINVAL
     assert lib.rfps_status_read(None, None) == EINVAL
+    sink = ctypes.c_void_p(256)
+    assert lib.rfps_bandwidth_probe(2, fake, 4096, 1, sink, None, None, None) == EINVAL       # no kind 2
+    assert lib.rfps_bandwidth_probe(0, fake, 4096, 0, sink, None, None, None) == EINVAL       # reps = 0
+    assert lib.rfps_bandwidth_probe(1, None, 0, 1 << 21, sink, None, None, None) == EINVAL    # reps > 2^20
+    assert lib.rfps_bandwidth_probe(0, None, 4096, 1, sink, None, None, None) == EINVAL       # no buffer
+    assert lib.rfps_bandwidth_probe(0, ctypes.c_void_p(264), 4096, 1, sink, None, None, None) == EINVAL
+    assert lib.rfps_bandwidth_probe(0, fake, 4100, 1, sink, None, None, None) == EINVAL       # not x16
+    assert lib.rfps_bandwidth_probe(1, None, 0, 1, None, None, None, None) == EINVAL          # no sink
+    assert lib.rfps_bandwidth_probe(1, None, 0, 1, ctypes.c_void_p(260), None, None, None) == EINVAL
     lib.rfps_index_free(None)
 
 
