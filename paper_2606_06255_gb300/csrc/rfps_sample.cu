@@ -803,13 +803,36 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     }
                     // ---- selection: warp -> CTA -> cluster
                     __syncwarp();
+                    // 128-thread clusters: each lane loads its own candidate's coordinates (a visited
+                    // point's are in registers already) while the warp reduces, and the winner's arrive
+                    // by shuffle, one shuffle and a dependent shared load shorter than fetching the
+                    // winning record's best point after the reduction.  With 8 or 16 warps per CTA the
+                    // extra loads cost more than that (measured), so larger CTAs keep the fetch.
+                    constexpr bool OWN_XYZ = FAST && CLUSTER && NT == 128;
+                    float ox = 0.f, oy = 0.f, oz = 0.f;
+                    if constexpr (OWN_XYZ) {
+                        ox = px;
+                        oy = py;
+                        oz = pz;
+                        if (!ppt && prec != 0xffffffffu && RFPS_IN(prec < nloc)) {
+                            const float4 b4 = v.best[prec];
+                            ox = b4.x;
+                            oy = b4.y;
+                            oz = b4.z;
+                        }
+                    }
                     unsigned long long wk;
                     const int wl = warp_argmax_lane(pk, &wk);
-                    const uint32_t wr = __shfl_sync(0xffffffffu, prec, wl);
-                    bool wpt = false;                 // the warp's candidate is a point visited now
+                    const uint32_t wr = OWN_XYZ ? 0u : __shfl_sync(0xffffffffu, prec, wl);
+                    bool wpt = false;                 // the warp's candidate coordinates are in vxyz
                     float4 vxyz = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if constexpr (FAST && CLUSTER) {
-                        wpt = __shfl_sync(0xffffffffu, ppt, wl);
+                    if constexpr (OWN_XYZ) {
+                        wpt = true;
+                        vxyz.x = __shfl_sync(0xffffffffu, ox, wl);
+                        vxyz.y = __shfl_sync(0xffffffffu, oy, wl);
+                        vxyz.z = __shfl_sync(0xffffffffu, oz, wl);
+                    } else if constexpr (FAST && CLUSTER) {
+                        wpt = __shfl_sync(0xffffffffu, ppt, wl);   // the candidate is a point visited now
                         if (wpt) {
                             vxyz.x = __shfl_sync(0xffffffffu, px, wl);
                             vxyz.y = __shfl_sync(0xffffffffu, py, wl);
