@@ -890,20 +890,36 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             // and the other warps of the cluster time out in turn (each wait bounded)
                             if (FAST) break;
                         }
+                        // 128-thread CTAs load each slot's coordinates with its key, and the winner's
+                        // arrive by shuffle instead of a shared load after the reduction (measured
+                        // faster there, slower with 256 threads, whose lanes read four slots each)
+                        constexpr bool SLOT_XYZ = NT == 128;
                         unsigned long long kk = 0ull;
                         uint32_t ki = 0;
+                        float4 kx = make_float4(0.f, 0.f, 0.f, 0.f);
     #pragma unroll
                         for (int u = 0; u < NSLOT / 32; ++u) {   // every slot, unrolled; unused ones read as 0
                             const uint32_t q = static_cast<uint32_t>(u * 32 + lane);
                             const unsigned long long x = q < nslot ? s_ckey[buf][q] : 0ull;
+                            float4 xq = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if constexpr (SLOT_XYZ) {
+                                if (q < nslot) xq = s_cxyz[buf][q];
+                            }
                             if (x > kk) {
                                 kk = x;
                                 ki = q;
+                                kx = xq;
                             }
                         }
                         const int gl = warp_argmax_lane(kk, &gbest);
-                        ki = __shfl_sync(0xffffffffu, ki, gl);
-                        cxyz = s_cxyz[buf][ki];
+                        if constexpr (SLOT_XYZ) {
+                            cxyz.x = __shfl_sync(0xffffffffu, kx.x, gl);
+                            cxyz.y = __shfl_sync(0xffffffffu, kx.y, gl);
+                            cxyz.z = __shfl_sync(0xffffffffu, kx.z, gl);
+                        } else {
+                            ki = __shfl_sync(0xffffffffu, ki, gl);
+                            cxyz = s_cxyz[buf][ki];
+                        }
                     }
                     sx = cxyz.x;
                     sy = cxyz.y;
