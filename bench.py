@@ -3,9 +3,16 @@
 A step is one full pass of the path over one cloud: device-side voxel index
 build (bounding box, binning, sort, records) plus the persistent sampling
 kernel (initial update, then M - 1 select / prune / skip / update / resync
-iterations).  Default workload: the room-like cloud, N = 100,000 points,
-M = 25,000 samples, start 0 (synthetic stand-in for the paper's indoor
-scans).  Other workloads: --workload uniform4k | lidar1m.
+iterations).  Default workload: the accumulated rotating-LiDAR scan,
+N = 1,124,730 points, M = 16,384 samples, start 0 (synthetic stand-in for the
+paper's outdoor scenes, Sec. Computation Efficiency and Resource
+Consumption), with the launch shape and voxel resolution picked by the
+autotuner before the timed region.  The same line carries, as extra keys,
+the room-like (N = 100,000, M = 25,000) and uniform (N = 4,096, M = 1,024)
+single clouds, the 64-cloud ragged batch (clouds/s, graph-replayed batch
+against per-cloud launches) and the Poisson serving run (p50 / p99 latency
+at 200 clouds/s offered); --secondary none leaves them out.  Other headline
+workloads: --workload uniform4k | room100k | batch64 | serving.
 
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
 on the launching stream; between steps a 256 MiB buffer is written to flush
@@ -13,8 +20,14 @@ the 129 MB L2 (outside the events).  Barrier + synchronize on both sides of
 the timed loop, max over ranks.  Multi-GPU: one process per GPU, each samples
 its own cloud (clouds are independent units; no data-path collective).
 
+The CPU baseline is the oracle as it stands, timed in a separate process
+that holds no CUDA context, after the GPU work: plain FPS on every host core
+(OpenMP) over the full workload, plain FPS on one thread over the first
+samples of the workload, and the CPU RadiusFPS on one thread at the paper's
+v = 32 (Sec. Hardware Acceleration and Parameter Sensitivity).
+
 --impl reference times the CPU oracle (plain FPS, all host cores) on the
-same workload instead (rank 0 only).
+same workload and config instead (rank 0 only).
 """
 
 from __future__ import annotations
@@ -23,6 +36,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -36,18 +50,21 @@ import numpy as np  # noqa: E402
 
 METRIC = "samples/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+SINGLE = ("lidar1m", "room100k", "uniform4k")
+L2_NOTE = "GPU arm: L2 flushed between timed steps (256 MiB write)"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="room100k",
-                    choices=["room100k", "uniform4k", "lidar1m", "batch64", "serving"])
+    ap.add_argument("--workload", default="lidar1m", choices=["lidar1m", "room100k", "uniform4k", "batch64", "serving"])
+    ap.add_argument("--secondary", default="uniform4k,room100k,batch64,serving",
+                    help="comma list of extra workloads measured into the same line (N = 1 only), or 'none'")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: offered clouds per second")
-    ap.add_argument("--requests", type=int, default=600, help="serving: timed requests")
+    ap.add_argument("--requests", type=int, default=1500, help="serving: timed requests")
     ap.add_argument("--slots", type=int, default=32, help="serving: micro-batches in flight (one stream each)")
     ap.add_argument("--max-batch", type=int, default=8, help="serving: clouds per micro-batch")
     ap.add_argument("--opts", default="", help="JSON dict of rfps_opts overrides")
@@ -61,7 +78,8 @@ def parse():
                     help="latency / memory vs M, prune-skip ablation, or voxel-resolution sensitivity on --workload")
     ap.add_argument("--once", action="store_true",
                     help="run the path once on the workload and exit (the case profiled with ncu)")
-    return ap.parse_args()
+    ap.add_argument("--cpu-timing", action="store_true", help=argparse.SUPPRESS)   # the CPU-baseline subprocess
+    return ap.parse_args(argv)
 
 
 def dist_setup(args):
@@ -158,9 +176,11 @@ class ClockSampler:
                 "window": "adjacent" if adjacent else "timed"}
 
 
-# launch shapes the single-cloud benchmark lets the autotuner choose between
-TUNE_CANDIDATES = [{"cluster": 16, "threads": 256}, {"cluster": 16, "threads": 128}, {"cluster": 8, "threads": 256},
-                   {"cluster": 16, "threads": 256, "chunk": 256}]
+# What the autotuner searches (paper_2606_06255_gb300.autotune.candidate_space(); a CPU test keeps the
+# two in step).  Stated here so that both arms print the same config without loading the library.
+TUNER_SPACE = ("stage 1: 33 launch shapes (cluster 1-16, threads 128/256/512, chunk 64/128/256) at the automatic "
+               "resolution; stage 2: the best 2 shapes x nvox_scale [35, 50, 70, 100, 140] "
+               "(n_vox = scale/100 * cbrt(N) per cloud)")
 
 
 def kernel_hash():
@@ -184,18 +204,29 @@ def ncu_traffic(workload, opts):
     return d.get("dram_bytes_per_launch")
 
 
-def cpu_threads():
-    import oracle
-    return oracle.openmp_threads() or 1
+def workload_config(name, seed=0):
+    """(clouds, config dict) of a workload; both arms print this config."""
+    import cloudgen
+    if name == "serving":
+        return None, {"workload": "serving", "sizes": "N log-uniform [20000, 1200000], M = N/8, half room / half LiDAR",
+                      "arrivals": "Poisson", "l2": L2_NOTE}
+    clouds, desc = cloudgen.workload(name, seed=seed)
+    if name == "batch64":
+        return clouds, {"workload": name, "desc": desc, "clouds": len(clouds),
+                        "points": int(sum(c.points.shape[0] for c in clouds)), "samples": int(sum(c.m for c in clouds)),
+                        "l2": L2_NOTE, "autotune_space": TUNER_SPACE}
+    c = clouds[0]
+    return clouds, {"workload": name, "desc": desc, "n": int(c.points.shape[0]), "m": int(c.m), "start": int(c.start),
+                    "clouds_per_gpu_per_step": 1, "l2": L2_NOTE, "autotune_space": TUNER_SPACE}
 
 
-def time_oracle(cloud, budget_s=10.0, max_s=30.0):
-    """The oracle as it stands (plain FPS, every host core) on the full workload, repeated ~10 s."""
+def time_oracle(cloud, budget_s=10.0, max_s=30.0, threads=0):
+    """The oracle as it stands (plain FPS, every host core by default) on the full workload, repeated ~10 s."""
     import oracle
     reps, t_total = 0, 0.0
     while t_total < budget_s and reps < 1000:
         t0 = time.perf_counter()
-        oracle.fps(cloud.points, cloud.m, cloud.start, threads=0)
+        oracle.fps(cloud.points, cloud.m, cloud.start, threads=threads)
         t_total += time.perf_counter() - t0
         reps += 1
         if t_total > max_s:
@@ -203,31 +234,91 @@ def time_oracle(cloud, budget_s=10.0, max_s=30.0):
     return reps, t_total
 
 
+def placement():
+    return {"host": platform.machine(), "cpus": os.cpu_count(),
+            "omp_proc_bind": os.environ.get("OMP_PROC_BIND", "unset (threads not pinned)"),
+            "omp_num_threads": os.environ.get("OMP_NUM_THREADS", "unset (one per core)")}
+
+
+def cpu_timing(name, budget_s=10.0):
+    """The three CPU timings of the oracle on one single-cloud workload (run in a process of its own
+    that has no CUDA context): plain FPS with OpenMP over full runs, plain FPS on one thread over the
+    first samples (its per-iteration cost is the same at every step), and the CPU RadiusFPS of
+    Sec. 3.2-3.4 on one thread over a full run at the paper's v = 32."""
+    import oracle
+    clouds, _ = workload_config(name)
+    cloud = clouds[0]
+    n, m = cloud.points.shape[0], cloud.m
+    threads = oracle.openmp_threads() or 1
+    reps, secs = time_oracle(cloud, budget_s)
+    m1 = min(m, 2048)
+    t0 = time.perf_counter()
+    oracle.fps(cloud.points, m1, cloud.start, threads=1)
+    t1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.radiusfps(cloud.points, m, cloud.start, n_vox=32)
+    t2 = time.perf_counter() - t0
+    plain1 = m1 / t1
+    return {
+        "value": reps * m / secs, "unit": "samples/s", "cores": threads, "kind": "oracle",
+        "sample": f"{reps} full run(s) of the {name} workload (N={n}, M={m}), plain FPS oracle with OpenMP, "
+                  f"{secs:.1f} s, in a separate process without a CUDA context",
+        "placement": placement(),
+        "plain_1thread": {"value": plain1, "unit": "samples/s", "cores": 1,
+                          "sample": f"the first {m1} of the {m} samples ({t1:.1f} s; plain FPS costs the same "
+                                    "per sample at every step)"},
+        "radiusfps_1thread": {"value": m / t2, "unit": "samples/s", "cores": 1, "n_vox": 32,
+                              "sample": f"one full run ({t2:.2f} s), CPU RadiusFPS oracle (prune + skip)",
+                              "speedup_vs_plain_1thread": (m / t2) / plain1},
+    }
+
+
+def cpu_baseline_subprocess(name):
+    """cpu_timing() in a fresh interpreter (no torch, no CUDA context); None if it fails."""
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-timing", "--workload", name],
+                           capture_output=True, text=True, timeout=600)
+        if r.returncode != 0:
+            return {"error": (r.stderr or r.stdout)[-300:]}
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except (subprocess.TimeoutExpired, ValueError, IndexError) as e:
+        return {"error": str(e)}
+
+
 def run_reference(args, rank):
+    """The oracle (plain FPS, every host core) as the reference arm: K timed steps of the same
+    workload and config as the GPU arm, on rank 0 only."""
     if rank != 0:
         return 0
-    import cloudgen
-    (cloud,), desc = cloudgen.workload(args.workload, seed=0)
-    threads = cpu_threads()
-    # warm-up, then K timed steps; each step one full oracle run of the workload
+    import oracle
+    clouds, config = workload_config(args.workload)
+    threads = oracle.openmp_threads() or 1
+    if clouds is None:   # serving: a bounded sample of the serving stream's clouds, one after another
+        import cloudgen
+        reqs = cloudgen.serving_requests(4, seed=0)
+        clouds = [c for _, c in reqs]
+    unit = "samples/s" if args.workload in SINGLE else "clouds/s"
+    step_clouds = clouds[:1] if args.workload in SINGLE else clouds
     for _ in range(min(args.warmup, 1)):
-        time_oracle(cloud, budget_s=0.0)
+        oracle.fps(step_clouds[0].points, step_clouds[0].m, step_clouds[0].start, threads=0)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        import oracle
-        oracle.fps(cloud.points, cloud.m, cloud.start, threads=0)
+        for c in step_clouds:
+            oracle.fps(c.points, c.m, c.start, threads=0)
         times.append(time.perf_counter() - t0)
     ms = 1e3 * statistics.mean(times)
-    value = cloud.m / (ms / 1e3)
+    per_step = step_clouds[0].m if unit == "samples/s" else len(step_clouds)
+    value = per_step / (ms / 1e3)
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": desc, "n": int(cloud.points.shape[0]), "m": cloud.m},
-        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": threads, "kind": "oracle",
-                         "sample": f"full {args.workload} workload per step (plain FPS oracle, OpenMP)"},
-        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "impl": "reference", "metric": METRIC if unit == "samples/s" else "clouds/s", "value": value, "unit": unit,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config,
+        "cpu_baseline": {"value": value, "unit": unit, "cores": threads, "kind": "oracle",
+                         "sample": f"full {args.workload} workload per step (plain FPS oracle, OpenMP)",
+                         "placement": placement()},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -292,15 +383,15 @@ def run_study(args, rf, torch, cloud, pts, opts):
     return 0
 
 
-def run_batch64(args, rf, torch, world=1, rank=0):
+def measure_batch64(args, rf, torch, world=1, rank=0):
     """64 ragged clouds: one graph-replayed batched launch vs 64 per-cloud launches vs plain batched.
 
     Under torchrun the clouds are sharded over the ranks (largest work first, no data-path
     collective); each rank samples its share as one batch, and the batch time is the slowest
-    rank's (strong scaling: the 64 clouds are the whole job)."""
-    import cloudgen
+    rank's (strong scaling: the 64 clouds are the whole job).  Returns the result dict on rank 0
+    (None on the other ranks)."""
     from paper_2606_06255_gb300 import shard
-    all_clouds, desc = cloudgen.workload("batch64")
+    all_clouds, config = workload_config("batch64")
     mine = shard.my_clouds([c.points.shape[0] for c in all_clouds], [c.m for c in all_clouds], world, rank)
     clouds = [all_clouds[b] for b in mine]
     sizes = [c.points.shape[0] for c in clouds]
@@ -310,11 +401,11 @@ def run_batch64(args, rf, torch, world=1, rank=0):
     if args.opts:
         opts = json.loads(args.opts)
     else:
-        # launch shape picked by the autotuner on this batch (cluster size, CTA threads, record
-        # chunk; the voxel resolution follows each cloud's size); every candidate gives the same indices
+        # launch shape and automatic-resolution scale picked by the autotuner on this batch (the
+        # voxel resolution follows each cloud's size); every candidate gives the same indices
         cat0 = torch.from_numpy(np.ascontiguousarray(np.concatenate([c.points for c in clouds]), np.float32)).cuda()
         opts, table = rf.autotune.tune_batch(cat0, sizes, ms, reps=2)
-        tuned = [{"ms": round(t, 3), "opts": o} for t, o in table]
+        tuned = [{"ms": round(t, 3), "opts": o} for t, o in table[:8]]
         del cat0
     bs = rf.batch.BatchSampler(sizes, ms, opts=opts)
     bs.load([c.points for c in clouds])
@@ -330,14 +421,12 @@ def run_batch64(args, rf, torch, world=1, rank=0):
         t = torch.tensor([t_batch], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_batch = float(t.item())
-        if rank == 0:
-            print(json.dumps({
-                "metric": "clouds/s", "value": len(all_clouds) / (t_batch / 1e3), "unit": "clouds/s",
-                "workload": "batch64", "desc": desc, "n_gpus": world, "scaling": "strong",
-                "clouds": len(all_clouds), "clouds_rank0": len(clouds), "ms_per_batch": t_batch,
-                "samples_per_s": sum(c.m for c in all_clouds) / (t_batch / 1e3), "opts_rank0": opts,
-                "graph": True, "gpu_launches_per_batch_rank0": launches}), flush=True)
-        return 0
+        if rank != 0:
+            return None
+        return {"metric": "clouds/s", "value": len(all_clouds) / (t_batch / 1e3), "unit": "clouds/s",
+                "config": config, "n_gpus": world, "scaling": "strong", "clouds_rank0": len(clouds),
+                "ms_per_batch": t_batch, "samples_per_s": sum(c.m for c in all_clouds) / (t_batch / 1e3),
+                "opts_rank0": opts, "graph": True, "gpu_launches_per_batch_rank0": launches}
     ref = bs.out.cpu().numpy()
     cat, off = bs.points, bs.offsets
     views = [cat[int(off[b]):int(off[b + 1])] for b in range(len(sizes))]
@@ -357,18 +446,15 @@ def run_batch64(args, rf, torch, world=1, rank=0):
         t = _events(torch, lambda: res.setdefault("o", rf.plain_fps_batched(cat, sizes, ms, variant=v, workspace=pws,
                                                                            meta=bs.meta)[0]), 1, flush)
         plain[f"variant{v}"] = {"ms": t, "clouds_per_s": len(sizes) / (t / 1e3)}
-    print(json.dumps({
-        "metric": "clouds/s", "value": len(sizes) / (t_batch / 1e3), "unit": "clouds/s", "workload": "batch64",
-        "desc": desc, "clouds": len(sizes), "points": int(sum(sizes)), "samples": int(sum(ms)),
-        "ms_per_batch": t_batch, "samples_per_s": sum(ms) / (t_batch / 1e3), "opts": opts, "autotune": tuned,
-        "graph": True,
-        "gpu_launches_per_batch": launches,
-        "per_cloud_launches": {"ms": t_sep, "clouds_per_s": len(sizes) / (t_sep / 1e3), "same_indices": same},
-        "batched_vs_per_cloud": t_sep / t_batch, "plain_batched": plain}), flush=True)
-    return 0
+    return {"metric": "clouds/s", "value": len(sizes) / (t_batch / 1e3), "unit": "clouds/s", "config": config,
+            "ms_per_batch": t_batch, "samples_per_s": sum(ms) / (t_batch / 1e3), "opts": opts, "autotune": tuned,
+            "graph": True, "gpu_launches_per_batch": launches,
+            "per_cloud_launches": {"ms": t_sep, "clouds_per_s": len(sizes) / (t_sep / 1e3), "same_indices": same},
+            "batched_vs_per_cloud": t_sep / t_batch, "plain_batched": plain,
+            "batched_vs_plain_batched": min(p["ms"] for p in plain.values()) / t_batch}
 
 
-def run_serving(args, rf, world=1, rank=0):
+def measure_serving(args, rf, world=1, rank=0):
     """Poisson request stream through the continuous-batching server.  Under torchrun the stream
     is sharded round-robin over the ranks, each serving its share on its own GPU; rank 0 merges
     the outcomes (latency percentiles and throughput over the whole stream)."""
@@ -391,60 +477,51 @@ def run_serving(args, rf, world=1, rank=0):
         parts = [None] * world
         dist.all_gather_object(parts, rep)
         if rank != 0:
-            return 0
+            return None
         rep = serve.merge_reports(parts)
     out = rep.summary()
     out["n_gpus"] = world
     out.update({"metric": "p99 latency / clouds/s", "workload": "serving", "offered_rate": args.rate,
                 "requests": args.requests, "opts": opts, "slots": args.slots, "max_batch": args.max_batch,
                 "sizes": "N log-uniform [20000, 1200000], M = N/8, half room / half LiDAR"})
-    print(json.dumps(out), flush=True)
-    return 0
+    return out
 
 
-def main():
-    args = parse()
-    world, rank, local = dist_setup(args)
-    if args.impl == "reference":
-        return run_reference(args, rank)
+def _timed_steps(torch, fn, steps, flush, stream):
+    """K steps of fn, each between CUDA events on `stream`, L2 flushed before each (outside the events)."""
+    evs = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
 
-    import torch
-    import torch.distributed as dist
 
-    import cloudgen
-    import paper_2606_06255_gb300 as rf
-
-    torch.cuda.set_device(local)
-    if args.floor_sweep:
-        for cluster in (1, 2, 4, 8, 16):
-            for threads in (128, 256, 512):
-                ms = min(rf.sync_floor(cluster, threads, 25000) for _ in range(3))
-                print(json.dumps({"cluster": cluster, "threads": threads, "ns_per_iteration": ms * 1e6 / 24999}),
-                      flush=True)
-        return 0
-    if world > 1 and not args.floor_sweep:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if args.workload == "batch64":
-        rc = run_batch64(args, rf, torch, world, rank)
-    elif args.workload == "serving":
-        rc = run_serving(args, rf, world, rank)
-    else:
-        rc = None
-    if rc is not None:
-        if world > 1:
-            dist.destroy_process_group()
-        return rc
+def measure_single(args, rf, torch, name, world=1, rank=0, local=0, full=True):
+    """One single-cloud workload: autotuned launch shape, K timed steps (index build + sampling), the
+    sampling kernel alone against its exchange floor, and the plain GPU FPS baselines on the same
+    cloud.  full=True (the headline) adds the clock record, work counters, roofline, on-chip probes
+    and the end-to-end run through the C ABI with host buffers."""
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
     dev = torch.device("cuda", local)
-    (cloud,), desc = cloudgen.workload(args.workload, seed=rank)
+    clouds, config = workload_config(name, seed=rank)
+    cloud = clouds[0]
     n, m, start = cloud.points.shape[0], cloud.m, cloud.start
-    opts = json.loads(args.opts) if args.opts else None
+    opts = json.loads(args.opts) if (args.opts and full) else None
     pts = torch.from_numpy(cloud.points).to(dev)
     tuned = None
-    if opts is None and not (args.no_tune or args.once or args.study):
-        # launch shape from the autotuner, timed on this cloud before (outside) the timed region;
-        # every candidate returns the same indices
-        opts, table = rf.autotune.tune_single(pts, m, start, candidates=TUNE_CANDIDATES, reps=3)
-        tuned = [{"ms": round(t, 3), "opts": o} for t, o in table]
+    if opts is None and not args.no_tune:
+        # launch shape, then voxel resolution, from the autotuner, timed on this cloud before (outside)
+        # the timed region; every candidate returns the same indices
+        opts, table = rf.autotune.tune_single(pts, m, start, reps=3)
+        tuned = [{"ms": round(t, 3), "opts": o} for t, o in table[:10]]
     ws = torch.empty(rf.workspace_size(n, opts), dtype=torch.uint8, device=dev)
     out = torch.empty(m, dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -453,69 +530,73 @@ def main():
     def step():
         rf.fps(pts, m, start, opts=opts, workspace=ws, out=out)
 
-    if args.study:
-        return run_study(args, rf, torch, cloud, pts, opts)
-
-    if args.once:
-        step()
-        torch.cuda.synchronize()
-        if rf.status(ws) != 0:
-            raise RuntimeError("device status %d" % rf.status(ws))
-        print(json.dumps({"once": args.workload, "n": n, "m": m, "first": out[:4].tolist()}), flush=True)
-        return 0
-
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
     if rf.status(ws) != 0:
         raise RuntimeError("device status after warm-up: %d" % rf.status(ws))
 
-    clocks = ClockSampler(local)
-    clocks.start()
-    if world > 1:
+    clocks = ClockSampler(local) if full else None
+    if clocks:
+        clocks.start()
+    if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.mark()
+    if clocks:
+        clocks.mark()
     launches0 = rf.launch_count()
-    evs = []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        evs.append((e0, e1))
-    torch.cuda.synchronize()
+    step_ms = _timed_steps(torch, step, args.steps if full else min(args.steps, 10), flush, stream)
     launches = rf.launch_count() - launches0
-    if world > 1:
+    if dist:
         dist.barrier()
-    clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
+    clk = clocks.stop() if clocks else None
     total_ms = sum(step_ms)
-    if world > 1:
+    if dist:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * args.steps * m / (total_ms / 1e3)
+    ms_per_step = total_ms / len(step_ms)
+    value = world * m / (ms_per_step / 1e3)
 
-    # ---- the sampling kernel alone (index path: tiny re-arm kernel + k_sample), for the roofline
+    # ---- the sampling kernel alone (index path: tiny re-arm kernel + k_sample) against its exchange floor
     ix = rf.Index(pts, opts=opts)
+    n_vox = ix.export()["n_vox"]
     for _ in range(2):
         ix.sample(m, start, out=out)
-    sample_ms = []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ix.sample(m, start, out=out)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        sample_ms.append(e0.elapsed_time(e1))
+    k_ms = statistics.mean(_timed_steps(torch, lambda: ix.sample(m, start, out=out), min(args.steps, 5), flush,
+                                        stream))
     ix.free()
-    k_ms = statistics.mean(sample_ms)
+    rs = rf.resolved_opts(n, opts)
+    floor_ms = min(rf.sync_floor(rs["cluster"], rs["threads"], max(2, m)) for _ in range(3))
+    ns_iter = k_ms * 1e6 / max(1, m - 1)
+    floor_ns = floor_ms * 1e6 / max(1, m - 1)
+
+    # ---- plain GPU FPS on the same cloud: cluster-resident (variant 1), whole GPU (variant 2), one CTA (0)
+    plain = None
+    if not args.no_plain:
+        plain = {}
+        pws = torch.empty(rf.plain_workspace_size(n), dtype=torch.uint8, device=dev)
+        for variant, label in ((1, "cluster"), (2, "whole_gpu"), (0, "one_cta_per_cloud")):
+            rf.plain_fps(pts, m, start, variant=variant, workspace=pws, out=out)
+            torch.cuda.synchronize()
+            reps = 1 if (variant == 0 and n > 50000) else max(2, min(args.steps, 3))
+            pm = statistics.mean(_timed_steps(
+                torch, lambda: rf.plain_fps(pts, m, start, variant=variant, workspace=pws, out=out), reps, flush, stream))
+            plain[label] = {"variant": variant, "ms_per_cloud": pm, "samples_per_s": m / (pm / 1e3),
+                            "radiusfps_speedup": pm / ms_per_step,
+                            # 16 B (coordinates + d2) per point per iteration, index build included
+                            "achieved_gbs": 16 * n * (m - 1) / (pm / 1e3) / 1e9}
+    res = {"config": config, "ms_per_cloud": ms_per_step, "samples_per_s": value, "opts": opts or "default",
+           "autotune": tuned, "n_vox": n_vox, "launch_shape": {"cluster": rs["cluster"], "threads": rs["threads"],
+                                                               "chunk": rs["chunk"]},
+           "kernel_ms": k_ms, "ns_per_iteration": ns_iter, "sync_floor_ns_per_iteration": floor_ns,
+           "plain_gpu_fps": plain}
+    if plain:
+        best = min(plain.values(), key=lambda p: p["ms_per_cloud"])
+        res["best_plain"] = {"variant": best["variant"], "ms_per_cloud": best["ms_per_cloud"],
+                             "radiusfps_speedup": best["radiusfps_speedup"]}
+    if not full:
+        return res
 
     # ---- algorithmic bytes of one sampling launch, from the work counters (untimed run)
     cws = torch.empty(rf.workspace_size(n, dict(opts or {}, counters=1)), dtype=torch.uint8, device=dev)
@@ -525,41 +606,13 @@ def main():
     alg_bytes = 32 * c["voxel_tests"] + 16 * c["points_visited"] + 4 * c["points_updated"] + 8 * resynced
     peak, peak_kind = load_peaks()
     achieved = alg_bytes / (k_ms / 1e3) / 1e9
-
-    # ---- per-iteration synchronisation floor of the launch shape the step used
-    rs = rf.resolved_opts(n, opts)
     # ---- on-chip roofline: after the first touch the loop's bytes come from shared memory and L2,
     # and one cloud occupies one cluster of SMs
     smem_bw = rf.bandwidth_probe("smem")
     l2_bw = rf.bandwidth_probe("l2")
     sms_used = rs["cluster"]
     onchip_peak = smem_bw["gbs_per_sm"] * sms_used
-    floor_ms = min(rf.sync_floor(rs["cluster"], rs["threads"], max(2, m)) for _ in range(3))
-    floor_ns = floor_ms * 1e6 / max(1, m - 1)
-
-    # ---- plain GPU FPS on the same cloud: cluster-resident (variant 1) and whole-GPU (variant 2)
-    plain = None
-    if not args.no_plain:
-        plain = {}
-        pws = torch.empty(rf.plain_workspace_size(n), dtype=torch.uint8, device=dev)
-        for variant, label in ((1, "cluster"), (2, "whole_gpu"), (0, "one_cta_per_cloud")):
-            rf.plain_fps(pts, m, start, variant=variant, workspace=pws, out=out)
-            torch.cuda.synchronize()
-            p_ms = []
-            for _ in range(1 if variant == 0 else max(2, min(args.steps, 3))):
-                flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                rf.plain_fps(pts, m, start, variant=variant, workspace=pws, out=out)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                p_ms.append(e0.elapsed_time(e1))
-            pm = statistics.mean(p_ms)
-            plain[label] = {"variant": variant, "ms_per_cloud": pm, "samples_per_s": m / (pm / 1e3),
-                            "radiusfps_speedup": pm / ms_per_step,
-                            # 16 B (coordinates + d2) per point per iteration, index build included
-                            "achieved_gbs": 16 * n * (m - 1) / (pm / 1e3) / 1e9}
+    min_floor_ns = min(rf.sync_floor(1, 128, max(2, m)) for _ in range(3)) * 1e6 / max(1, m - 1)
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     host_pts = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
@@ -575,48 +628,105 @@ def main():
         rf.fps_host(hp, m, start, opts=opts, workspace=hws)
         e2e_s.append(time.perf_counter() - t0)
     e2e_mean = statistics.mean(e2e_s)
-    if world > 1:   # the slowest rank, as for the device-timed value
+    if dist:   # the slowest rank, as for the device-timed value
         t = torch.tensor([e2e_mean], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_mean = float(t.item())
-    e2e_value = world * m / e2e_mean
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        reps, secs = time_oracle(cloud)
-        cpu = {"value": reps * m / secs, "unit": "samples/s", "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"{reps} full run(s) of the {args.workload} workload (N={n}, M={m}), "
-                         f"plain FPS oracle with OpenMP, {secs:.1f} s"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": len(step_ms),
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config,
+        "ms_per_cloud": ms_per_step,
+        "launch": {"opts": opts or "default", "n_vox": n_vox, "shape": res["launch_shape"], "autotune": tuned},
+        "plain_gpu_fps": plain,
+        "best_plain": res.get("best_plain"),
+        # The sampling loop is bound by the per-iteration cluster exchange, not by bandwidth: its
+        # headline efficiency is the exchange floor of its launch shape over the time per iteration.
+        "roofline": {"bound": "latency", "achieved": 1e9 / ns_iter, "peak": 1e9 / floor_ns, "unit": "iterations/s",
+                     "frac": floor_ns / ns_iter, "traffic": ncu_traffic(name, opts),
+                     "kernel": "k_sample", "kernel_ms": k_ms,
+                     "ns_per_iteration": ns_iter, "sync_floor_ns_per_iteration": floor_ns,
+                     "peak_kind": "per-iteration exchange floor of the same launch shape, measured by rfps_sync_floor "
+                                  "in this run",
+                     "min_floor_ns_per_iteration": min_floor_ns, "launch_shape": res["launch_shape"],
+                     "hbm": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                             "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
+                             "traffic": ncu_traffic(name, opts)},
+                     "onchip": {"bound": "smem", "sms_used": sms_used, "achieved": achieved, "peak": onchip_peak,
+                                "unit": "GB/s", "frac": achieved / onchip_peak,
+                                "smem_gbs_per_sm": smem_bw["gbs_per_sm"], "smem_gbs": smem_bw["gbs"],
+                                "l2_gbs": l2_bw["gbs"], "l2_probe_bytes": l2_bw["buffer_bytes"],
+                                "peak_kind": "measured by rfps_bandwidth_probe in this run"}},
+        "counters": c,
+        "cpu_baseline": None,
+        "e2e": {"value": world * m / e2e_mean, "unit": "samples/s", "h2d_bytes_per_step": n * 12,
+                "d2h_bytes_per_step": m * 8},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    return line if rank == 0 else None
 
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": desc, "n": n, "m": m, "start": start,
-                       "clouds_per_gpu_per_step": 1, "l2": "flushed between steps (256 MiB write)",
-                       "opts": opts or "default", "autotune": tuned},
-            "ms_per_cloud": ms_per_step,
-            "plain_gpu_fps": plain,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": ncu_traffic(args.workload, opts),
-                         "kernel": "k_sample", "kernel_ms": k_ms, "alg_bytes_per_launch": alg_bytes,
-                         "peak_kind": peak_kind,
-                         "ns_per_iteration": k_ms * 1e6 / max(1, m - 1),
-                         "sync_floor_ns_per_iteration": floor_ns,
-                         "launch_shape": {"cluster": rs["cluster"], "threads": rs["threads"]},
-                         "onchip": {"bound": "smem", "sms_used": sms_used, "peak": onchip_peak, "unit": "GB/s",
-                                    "frac": achieved / onchip_peak,
-                                    "smem_gbs_per_sm": smem_bw["gbs_per_sm"], "smem_gbs": smem_bw["gbs"],
-                                    "l2_gbs": l2_bw["gbs"], "l2_probe_bytes": l2_bw["buffer_bytes"],
-                                    "peak_kind": "measured by rfps_bandwidth_probe in this run"}},
-            "counters": c,
-            "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": n * 12,
-                    "d2h_bytes_per_step": m * 8},
-            "gpu_launches": launches,
-            "clocks": clk,
-        }
+
+def main(argv=None):
+    args = parse(argv)
+    world, rank, local = dist_setup(args)
+    if args.cpu_timing:
+        print(json.dumps(cpu_timing(args.workload)), flush=True)
+        return 0
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2606_06255_gb300 as rf
+
+    torch.cuda.set_device(local)
+    if args.floor_sweep:
+        for cluster in (1, 2, 4, 8, 16):
+            for threads in (128, 256, 512):
+                ms = min(rf.sync_floor(cluster, threads, 25000) for _ in range(3))
+                print(json.dumps({"cluster": cluster, "threads": threads, "ns_per_iteration": ms * 1e6 / 24999}),
+                      flush=True)
+        return 0
+    if args.study or args.once:
+        if args.workload not in SINGLE:
+            raise SystemExit("--study / --once take a single-cloud workload")
+        (cloud,), _ = workload_config(args.workload)
+        pts = torch.from_numpy(cloud.points).cuda()
+        opts = json.loads(args.opts) if args.opts else None
+        if args.study:
+            return run_study(args, rf, torch, cloud, pts, opts)
+        ws = torch.empty(rf.workspace_size(pts.shape[0], opts), dtype=torch.uint8, device="cuda")
+        out = rf.fps(pts, cloud.m, cloud.start, opts=opts, workspace=ws)
+        torch.cuda.synchronize()
+        if rf.status(ws) != 0:
+            raise RuntimeError("device status %d" % rf.status(ws))
+        print(json.dumps({"once": args.workload, "n": pts.shape[0], "m": cloud.m, "first": out[:4].tolist()}),
+              flush=True)
+        return 0
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "batch64":
+        line = measure_batch64(args, rf, torch, world, rank)
+    elif args.workload == "serving":
+        line = measure_serving(args, rf, world, rank)
+    else:
+        line = measure_single(args, rf, torch, args.workload, world, rank, local, full=True)
+    if line is not None and world == 1 and args.secondary != "none":
+        # the other configurations, measured into the same line (each with its own timing)
+        for name in [s for s in args.secondary.split(",") if s and s != args.workload]:
+            if name in SINGLE:
+                line[name] = measure_single(args, rf, torch, name, full=False)
+            elif name == "batch64":
+                line[name] = measure_batch64(args, rf, torch)
+            elif name == "serving":
+                line[name] = measure_serving(args, rf)
+    if line is not None and args.workload in SINGLE and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_subprocess(args.workload)   # after the GPU work, in a clean process
+    if line is not None:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

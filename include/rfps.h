@@ -72,6 +72,9 @@ typedef struct {
                             1: the paper's sqrt(3)/2 * L (Eq. preprocess_voxel_radius),
                                raised to the measured value if rounding requires it */
     int32_t counters;    /* 1: accumulate work counters (rfps_counters_read); slower */
+    int32_t nvox_scale;  /* automatic resolution (n_vox = 0): each cloud gets
+                            n_vox = round(nvox_scale / 100 * cbrt(N)) bins per axis;
+                            0 means 70, valid 1..1000.  Ignored when n_vox > 0 */
 } rfps_opts;
 
 /* Work counters of the sampling loop (Fig. samplestep / Tab. ablation
@@ -94,9 +97,9 @@ void rfps_opts_default(rfps_opts *opts);
 
 /* The options a call on a cloud of n points will use, automatic fields
  * resolved (host only, no device work): threads 256, clusters of 16 CTAs
- * from 2,048 points up (1 below), records of at most 128 points; n_vox stays
- * 0 when automatic because the device picks it per cloud (about
- * 0.7 * cbrt(N)).  RFPS_EINVAL for invalid options. */
+ * from 2,048 points up (1 below), records of at most 128 points, nvox_scale
+ * 70; n_vox stays 0 when automatic because the device picks it per cloud
+ * (nvox_scale / 100 * cbrt(N)).  RFPS_EINVAL for invalid options. */
 rfps_status rfps_opts_resolve(int64_t n, const rfps_opts *in, rfps_opts *out);
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -137,6 +140,25 @@ rfps_status rfps_fps(const float *points, int64_t n, int64_t m, int64_t start,
                      int64_t *out_idx, const rfps_opts *opts, void *workspace,
                      size_t workspace_bytes, void *stream);
 
+/* rfps_fps_lost_round: a test of the device-side failure path of rfps_fps.
+ * The same call with work counters on, except that in sampling iteration
+ * `lost_iteration` (1 <= lost_iteration < M) no CTA sends its candidate to the
+ * cluster exchange (Sec. 4.2's per-iteration synchronisation), as if those
+ * messages were lost.  Every exchange wait of that iteration then gives up
+ * after `spin_limit` polls (1 .. 2^22; rfps_fps uses 2^22), the launch records
+ * RFPS_ETIMEOUT in the workspace's status word (rfps_status_read) and the CTAs
+ * of the cluster leave the kernel together; out_idx is then unspecified.  No
+ * exchange message is in flight when the waits give up: every earlier
+ * iteration's messages have arrived (their waits completed) and the lost one
+ * sends none.  The workspace can be used again by the next call.  Needs a
+ * cluster of at least 2 CTAs (a single CTA has no exchange): RFPS_EINVAL
+ * otherwise, as for M < 2.  Other arguments and errors as rfps_fps. */
+rfps_status rfps_fps_lost_round(const float *points, int64_t n, int64_t m,
+                                int64_t start, int64_t *out_idx,
+                                const rfps_opts *opts, void *workspace,
+                                size_t workspace_bytes, int64_t lost_iteration,
+                                uint32_t spin_limit, void *stream);
+
 /* rfps_fps_host: the same call on HOST buffers.  Copies the points into the
  * workspace (which must hold rfps_fps_host_workspace_size() bytes), samples,
  * copies the indices back to host_out, and synchronises `stream`.  Returns
@@ -158,13 +180,22 @@ rfps_status rfps_fps_host(const float *host_points, int64_t n, int64_t m,
  * default options, N above 725,440 points) is rejected with RFPS_ENOMEM.  Every call on a GPU
  * shares the one array: calls whose work overlaps on the GPU race, so
  * serialise them (one stream, or events).  The kernels reset the state they
- * need at the start of each call.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress) and should come before any
- * stream capture.  Device-side errors (a non-finite coordinate) are not
- * reported by this call; the output is then unspecified. */
+ * need at the start of each call.  Every call looks up the array's device
+ * address (cudaGetSymbolAddress) on the current device; the first call on a
+ * device may load the library's device code and should come before any stream
+ * capture.  Errors only the device can see (a non-finite coordinate, a
+ * cluster exchange wait that gave up) are not returned by this call: read
+ * them with rfps_noalloc_status_read, after which the output of a failed call
+ * is unspecified. */
 rfps_status rfps_fps_noalloc(const float *points, int64_t n, int64_t m,
                              int64_t start, int64_t *out_idx,
                              const rfps_opts *opts, void *stream);
+/* rfps_noalloc_status_read: the device status of the last rfps_fps_noalloc
+ * call on the current device (RFPS_OK if it recorded no error), read from the
+ * fixed array into a host variable; synchronises `stream`, which must be the
+ * stream of that call or ordered after it.  Allocates nothing.  The paper has
+ * no counterpart. */
+rfps_status rfps_noalloc_status_read(void *stream);
 
 /* ------------------------------------------------------------------------
  * Ragged batch: B clouds concatenated in one point array, sampled by one
@@ -308,6 +339,13 @@ rfps_status rfps_index_sample_more(rfps_index *index, int64_t m_more,
  * rfps_index_sample. */
 rfps_status rfps_index_distances(const rfps_index *index, float *d2_out,
                                  void *stream);
+/* rfps_index_status_copy: enqueues on `stream` a copy of the index's device
+ * status word (the first error recorded by its last build or sampling call,
+ * RFPS_OK if none; the same codes as rfps_status_read) into *host_status.
+ * Page-locked host memory keeps the copy asynchronous; read the value once
+ * the stream has passed this point (e.g. after an event recorded behind it). */
+rfps_status rfps_index_status_copy(const rfps_index *index,
+                                   int32_t *host_status, void *stream);
 size_t rfps_index_bytes(const rfps_index *index);
 void rfps_index_free(rfps_index *index);
 rfps_status rfps_index_export(const rfps_index *index, int64_t *n_records,

@@ -31,7 +31,7 @@ class Opts(ctypes.Structure):
     """rfps_opts: zero = automatic, except prune / skip (default 1)."""
     _fields_ = [("n_vox", ctypes.c_int32), ("cluster", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("prune", ctypes.c_int32), ("skip", ctypes.c_int32),
-                ("radius_mode", ctypes.c_int32), ("counters", ctypes.c_int32)]
+                ("radius_mode", ctypes.c_int32), ("counters", ctypes.c_int32), ("nvox_scale", ctypes.c_int32)]
 
     def __init__(self, **kw):
         super().__init__()
@@ -71,9 +71,11 @@ def _load():
         "rfps_launch_count": (i64, []),
         "rfps_fps_workspace_size": (sz, [i64, optp]),
         "rfps_fps": (st, [vp, i64, i64, i64, vp, optp, vp, sz, vp]),
+        "rfps_fps_lost_round": (st, [vp, i64, i64, i64, vp, optp, vp, sz, i64, ctypes.c_uint32, vp]),
         "rfps_fps_host_workspace_size": (sz, [i64, optp]),
         "rfps_fps_host": (st, [vp, i64, i64, i64, vp, optp, vp, sz, vp]),
         "rfps_fps_noalloc": (st, [vp, i64, i64, i64, vp, optp, vp]),
+        "rfps_noalloc_status_read": (st, [vp]),
         "rfps_batch_workspace_size": (sz, [i64, i64, i64, optp]),
         "rfps_fps_batched": (st, [vp, i64, vp, i64, vp, vp, i64, vp, optp, vp, sz, vp]),
         "rfps_plain_workspace_size": (sz, [i64, i64]),
@@ -88,6 +90,7 @@ def _load():
         "rfps_index_sample_more": (st, [vp, i64, vp, vp]),
         "rfps_index_distances": (st, [vp, vp, vp]),
         "rfps_index_bytes": (sz, [vp]),
+        "rfps_index_status_copy": (st, [vp, vp, vp]),
         "rfps_index_free": (None, [vp]),
         "rfps_index_export": (st, [vp, ctypes.POINTER(i64), vp, vp, vp, vp, vp, vp, ctypes.POINTER(i32)]),
     }
@@ -357,6 +360,20 @@ class Index:
         d2 = torch.empty(self.n, dtype=torch.float32, device=self.device)
         _check(_lib.rfps_index_distances(self._h, d2.data_ptr(), _stream(stream)), "rfps_index_distances")
         return d2
+
+    def status_into(self, host: torch.Tensor, stream=None):
+        """Enqueue a copy of the index's device status word into `host` (an int32 tensor of one
+        element, pinned for an asynchronous copy); valid once the stream has passed this point."""
+        if host.dtype != torch.int32 or host.numel() < 1 or host.is_cuda:
+            raise TypeError("host must be a CPU int32 tensor")
+        _check(_lib.rfps_index_status_copy(self._h, host.data_ptr(), _stream(stream)), "rfps_index_status_copy")
+
+    def status(self, stream=None) -> int:
+        """The index's device status word (synchronises the stream)."""
+        h = torch.zeros(1, dtype=torch.int32)
+        self.status_into(h, stream)
+        (stream or torch.cuda.current_stream()).synchronize()
+        return int(h[0])
 
     def export(self) -> dict:
         n = self.n

@@ -33,13 +33,32 @@ def key(kind: str, n: int, batch: int = 1) -> str:
     return f"{kind}:b{batch}:n{size_bucket(n)}"
 
 
+# automatic voxel resolutions tried after the launch shape: nvox_scale / 100 * cbrt(N) bins per
+# axis for every cloud (70 is the library default)
+NVOX_SCALES = (35, 50, 70, 100, 140)
+
+
 def default_candidates(batch: bool = False):
+    """Launch shapes (cluster size, CTA threads, record chunk) the first stage times.
+
+    Every cluster size the kernel supports is tried, with 128- and 256-thread CTAs and records of
+    64, 128 or 256 points; 512-thread CTAs only in clusters of up to 4 (their exchange floor grows
+    fastest with the cluster size)."""
     cands = []
-    for cluster in ((2, 4, 8, 16) if batch else (4, 8, 16)):
+    for cluster in (1, 2, 4, 8, 16):
         for threads in (128, 256, 512):
-            for chunk in (64, 128):
+            if threads == 512 and cluster > 4:
+                continue
+            for chunk in ((64, 128, 256) if threads < 512 else (128,)):
                 cands.append({"cluster": cluster, "threads": threads, "chunk": chunk})
     return cands
+
+
+def candidate_space(batch: bool = False) -> str:
+    """One-line description of what the tuner searches (for reports)."""
+    return (f"stage 1: {len(default_candidates(batch))} launch shapes (cluster 1-16, threads 128/256/512, "
+            f"chunk 64/128/256) at the automatic resolution; stage 2: the best 2 shapes x nvox_scale "
+            f"{list(NVOX_SCALES)} (n_vox = scale/100 * cbrt(N) per cloud)")
 
 
 def _time(fn, reps):
@@ -59,30 +78,49 @@ def _time(fn, reps):
     return statistics.median(ts)
 
 
-def tune_single(points: torch.Tensor, m: int, start: int = 0, candidates=None, reps: int = 3):
-    """Time each candidate on one cloud; returns (best opts, [(ms, opts), ...])."""
-    n = points.shape[0]
-    out = torch.empty(m, dtype=torch.int64, device=points.device)
-    rows = []
-    for o in candidates or default_candidates(False):
-        ws = torch.empty(_lib.workspace_size(n, o), dtype=torch.uint8, device=points.device)
-        ms = _time(lambda: _lib.fps(points, m, start, opts=o, workspace=ws, out=out), reps)
-        rows.append((ms, o))
+def _two_stage(time_one, candidates, scales, keep: int = 2):
+    """Stage 1 times every launch shape at the automatic resolution; stage 2 times the `keep`
+    fastest shapes at each automatic-resolution scale.  Returns (best opts, rows sorted by time)."""
+    rows = [(time_one(o), o) for o in candidates]
+    rows.sort(key=lambda r: r[0])
+    if not math.isfinite(rows[0][0]):
+        raise RuntimeError("autotune: no candidate ran without a device error")
+    for _, o in [r for r in rows if math.isfinite(r[0])][:keep]:
+        for sc in scales:
+            if sc == 70 or "n_vox" in o or "nvox_scale" in o:
+                continue
+            o2 = dict(o, nvox_scale=sc)
+            rows.append((time_one(o2), o2))
     rows.sort(key=lambda r: r[0])
     return rows[0][1], rows
 
 
-def tune_batch(points: torch.Tensor, sizes, ms, starts=None, candidates=None, reps: int = 3):
-    """Time each candidate on a ragged batch (one launch); returns (best opts, table)."""
+def tune_single(points: torch.Tensor, m: int, start: int = 0, candidates=None, reps: int = 3,
+                scales=NVOX_SCALES):
+    """Time launch shapes, then voxel resolutions, on one cloud; returns (best opts, [(ms, opts), ...]).
+    Pass scales=() to time the candidates only."""
+    n = points.shape[0]
+    out = torch.empty(m, dtype=torch.int64, device=points.device)
+
+    def time_one(o):
+        ws = torch.empty(_lib.workspace_size(n, o), dtype=torch.uint8, device=points.device)
+        ms = _time(lambda: _lib.fps(points, m, start, opts=o, workspace=ws, out=out), reps)
+        # a shape the device could not run on this cloud (e.g. more records than one CTA can index)
+        # records an error instead of sampling: never a candidate
+        return ms if _lib.status(ws) == 0 else math.inf
+    return _two_stage(time_one, candidates or default_candidates(False), scales)
+
+
+def tune_batch(points: torch.Tensor, sizes, ms, starts=None, candidates=None, reps: int = 3, scales=NVOX_SCALES):
+    """Time launch shapes, then voxel resolutions, on a ragged batch (one launch); returns (best opts, table)."""
     meta = _lib._batch_meta(sizes, ms, starts, points.device)
-    rows = []
-    for o in candidates or default_candidates(True):
+
+    def time_one(o):
         ws = torch.empty(_lib.batch_workspace_size(points.shape[0], len(sizes), max(sizes), o), dtype=torch.uint8,
                          device=points.device)
         t = _time(lambda: _lib.fps_batched(points, sizes, ms, starts, opts=o, workspace=ws, meta=meta), reps)
-        rows.append((t, o))
-    rows.sort(key=lambda r: r[0])
-    return rows[0][1], rows
+        return t if _lib.status(ws) == 0 else math.inf
+    return _two_stage(time_one, candidates or default_candidates(True), scales)
 
 
 def load_cache(path: str = DEFAULT_CACHE) -> dict:

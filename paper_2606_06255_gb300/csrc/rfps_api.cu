@@ -16,11 +16,12 @@ namespace rfps {
 namespace {
 std::atomic<int64_t> g_launches{0};
 
-// Cells per axis chosen when opts.n_vox == 0: about 0.7 * cbrt(N), the value
-// the device computes per cloud (k_setup); the host only needs an upper bound.
-int auto_nvox_bound(int64_t n, int cap)
+// Cells per axis chosen when opts.n_vox == 0: about nvox_scale / 100 * cbrt(N),
+// the value the device computes per cloud (k_setup); the host only needs an
+// upper bound.
+int auto_nvox_bound(int64_t n, int scale_pct, int cap)
 {
-    const double v = std::rint(0.7 * std::cbrt(static_cast<double>(n))) + 1.0;
+    const double v = std::rint(scale_pct / 100.0 * std::cbrt(static_cast<double>(n))) + 1.0;
     const int nv = static_cast<int>(v < 1.0 ? 1.0 : v);
     return nv < cap ? nv : cap;
 }
@@ -81,6 +82,7 @@ rfps_opts resolve_opts(const rfps_opts* in, int64_t max_n)
     if (o.threads != 128 && o.threads != 256 && o.threads != 512) o.threads = 256;
     if (o.cluster <= 0) o.cluster = max_n < 2048 ? 1 : 16;
     if (o.chunk <= 0) o.chunk = 128;
+    if (o.nvox_scale <= 0) o.nvox_scale = 70;
     return o;
 }
 
@@ -124,7 +126,7 @@ WsLayout make_layout(int64_t total_n, int64_t n_clouds, int64_t max_n, const rfp
     L.n_clouds = n_clouds;
     // sort key bits: global cell ids < n_clouds * n_vox_max^3
     const int cap = nvox_cap(n_clouds);
-    const int nv = o.n_vox > 0 ? std::min(o.n_vox, cap) : auto_nvox_bound(max_n, cap);
+    const int nv = o.n_vox > 0 ? std::min(o.n_vox, cap) : auto_nvox_bound(max_n, o.nvox_scale, cap);
     const double cells = std::ldexp(1.0, 3 * morton_bits(nv)) * static_cast<double>(n_clouds);
     int bits = 1;
     while (bits < 32 && std::ldexp(1.0, bits) < cells) ++bits;
@@ -180,6 +182,7 @@ static rfps_status check_opts(const rfps_opts* o)
     if (o->threads != 0 && o->threads != 128 && o->threads != 256 && o->threads != 512) return RFPS_EINVAL;
     if (o->chunk != 0 && (!is_pow2(o->chunk) || o->chunk < 32 || o->chunk > 4096)) return RFPS_EINVAL;
     if (o->radius_mode != 0 && o->radius_mode != 1) return RFPS_EINVAL;
+    if (o->nvox_scale < 0 || o->nvox_scale > 1000) return RFPS_EINVAL;
     return RFPS_OK;
 }
 
@@ -211,7 +214,7 @@ const char* rfps_status_str(int s)
     }
 }
 
-int rfps_version(void) { return 1; }
+int rfps_version(void) { return 2; }
 
 rfps_status rfps_opts_resolve(int64_t n, const rfps_opts* in, rfps_opts* out)
 {
@@ -250,6 +253,30 @@ rfps_status rfps_fps(const float* points, int64_t n, int64_t m, int64_t start, i
     cudaError_t e = launch_setup(ws, L, nullptr, nullptr, nullptr, 1, n, n, m, start, n, o, st);
     if (e == cudaSuccess) e = launch_build(ws, L, points, o, n, st);
     if (e == cudaSuccess) e = launch_sample(ws, L, points, out_idx, o, 1, n, st);
+    return from_cuda(e);
+}
+
+rfps_status rfps_fps_lost_round(const float* points, int64_t n, int64_t m, int64_t start, int64_t* out_idx,
+                                const rfps_opts* opts, void* workspace, size_t workspace_bytes, int64_t lost_iteration,
+                                uint32_t spin_limit, void* stream)
+{
+    if (!points || !out_idx || !workspace || n < 1 || n >= (int64_t(1) << 31) || m < 2 || m > n || start < 0 ||
+        start >= n || !aligned256(workspace) || lost_iteration < 1 || lost_iteration >= m || spin_limit < 1 ||
+        spin_limit > (1u << 22))
+        return RFPS_EINVAL;
+    rfps_status s = check_opts(opts);
+    if (s != RFPS_OK) return s;
+    if ((s = device_check()) != RFPS_OK) return s;
+    rfps_opts o = resolve_opts(opts, n);
+    if (o.cluster < 2) return RFPS_EINVAL;   // one CTA has no exchange to lose
+    o.counters = 1;
+    const WsLayout L = make_layout(n, 1, n, o, false, 0);
+    if (workspace_bytes < L.total) return RFPS_ENOMEM;
+    char* ws = static_cast<char*>(workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_setup(ws, L, nullptr, nullptr, nullptr, 1, n, n, m, start, n, o, st);
+    if (e == cudaSuccess) e = launch_build(ws, L, points, o, n, st);
+    if (e == cudaSuccess) e = launch_sample(ws, L, points, out_idx, o, 1, n, st, false, lost_iteration, spin_limit);
     return from_cuda(e);
 }
 
@@ -504,6 +531,14 @@ rfps_status rfps_index_distances(const rfps_index* ix, float* d2_out, void* stre
         d2_out);
     note_launches(1);
     return from_cuda(cudaGetLastError());
+}
+
+rfps_status rfps_index_status_copy(const rfps_index* ix, int32_t* host_status, void* stream)
+{
+    if (!ix || !host_status) return RFPS_EINVAL;
+    const WsHeader* h = reinterpret_cast<const WsHeader*>(static_cast<const char*>(ix->mem) + ix->L.header);
+    return from_cuda(cudaMemcpyAsync(host_status, &h->status, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                     static_cast<cudaStream_t>(stream)));
 }
 
 size_t rfps_index_bytes(const rfps_index* ix) { return ix ? ix->bytes : 0; }

@@ -544,7 +544,7 @@ cudaError_t launch_setup(char* ws, const WsLayout& L, const int64_t* offsets, co
     int cap = kMaxNVox;
     while (cap > 1 && std::ldexp(1.0, 3 * morton_bits(cap)) * static_cast<double>(n_clouds) >= 4294967295.0) --cap;
     k_setup<<<1, 256, 0, st>>>(hdr, clouds, order, offsets, out_offsets, starts, n_clouds, total_n, n, m, start,
-                               max_n, o.n_vox, cap, 0.7f, sort_clouds);
+                               max_n, o.n_vox, cap, static_cast<float>(o.nvox_scale) / 100.0f, sort_clouds);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -73,9 +73,11 @@ rfps_opts resolve_opts(const rfps_opts* in, int64_t max_n);
 cudaError_t launch_build(char* ws, const WsLayout& L, const float* points, const rfps_opts& o,
                          int64_t max_n, cudaStream_t st);
 // Persistent sampling launch over the clouds of ws.
+// lost_iter > 0 (failure-path test, counting kernels): exchange round lost_iter sends nothing and
+// its waits give up after spin_limit polls (0: the default limit).
 cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int64_t* out,
                           const rfps_opts& o, int64_t n_clouds, int64_t max_n, cudaStream_t st,
-                          bool save_state = false);
+                          bool save_state = false, int64_t lost_iter = 0, uint32_t spin_limit = 0);
 // Synchronisation floor of the sampling loop (same tail, no record work).
 cudaError_t launch_sync_floor(int C, int NT, int64_t iters, unsigned long long* sink, cudaStream_t st);
 // On-chip bandwidth probe (rfps_probe.cu): kind 0 L2 reads of `buf`, kind 1 shared-memory reads.

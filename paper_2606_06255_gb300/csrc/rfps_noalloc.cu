@@ -18,12 +18,18 @@
 // call, so no clearing is needed between calls.
 //
 // Host code cannot use the array's name as a device address (in host code it
-// names a host-side stand-in), so on the first call on each device, with that
-// device current, the address is looked up with cudaGetSymbolAddress and
-// cached.  That first call therefore performs a runtime query and should come
-// before any stream capture.
-#include <mutex>
-
+// names a host-side stand-in), so every call looks the address up with
+// cudaGetSymbolAddress, with the calling device current, and checks the return
+// code.  The lookup is not cached: after cudaDeviceReset, or in another CUDA
+// context on the same device, the module can be loaded at another address,
+// and a cached pointer would then address memory the array no longer occupies.
+// Once the module is loaded on a device the lookup allocates nothing; the first
+// call on each device may load it, so that first call should come before any
+// stream capture.
+//
+// Device-side errors (a non-finite coordinate, a cluster exchange wait that
+// gave up, a cloud too large for one CTA's index) are written to the status
+// word at the start of the array; rfps_noalloc_status_read returns it.
 #include "rfps_common.cuh"
 #include "rfps_internal.h"
 
@@ -31,28 +37,16 @@ namespace rfps {
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-std::mutex g_noalloc_mutex;
-void* g_noalloc_ptr[kMaxDevices] = {};
-
-// Device address of this device's scratch array (looked up once per device).
+// Device address of the current device's scratch array, looked up on every call.
 cudaError_t noalloc_scratch(void** out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (g_noalloc_ptr[dev] == nullptr) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = p;
-    }
-    *out = g_noalloc_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 
@@ -74,4 +68,16 @@ extern "C" rfps_status rfps_fps_noalloc(const float* points, int64_t n, int64_t 
     if (noalloc_scratch(&ws) != cudaSuccess) return RFPS_ECUDA;
     // the same launches as rfps_fps, on the fixed scratch instead of a caller workspace
     return rfps_fps(points, n, m, start, out_idx, opts, ws, kNoAllocScratchBytes, stream);
+}
+
+extern "C" rfps_status rfps_noalloc_status_read(void* stream)
+{
+    void* ws = nullptr;
+    if (noalloc_scratch(&ws) != cudaSuccess) return RFPS_ECUDA;
+    // the status word opens the workspace header; copied into a host local, then the stream is synchronised
+    uint32_t status = 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&status, ws, sizeof(status), cudaMemcpyDeviceToHost, st) != cudaSuccess) return RFPS_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return RFPS_ECUDA;
+    return static_cast<rfps_status>(status);
 }

@@ -56,6 +56,10 @@ struct SampleArgs {
     int prune, skip;
     int resident;              // 1: keep records' points in shared memory while they fit
     int save_state;            // 1: write the sampling state back at the end (resumable index)
+    // Failure-path test (counting kernels only): in exchange round `lost_iter` no warp sends its
+    // candidate, and each exchange wait gives up after `spin_limit` polls.  lost_iter 0: none.
+    int64_t lost_iter;
+    uint32_t spin_limit;
 #ifdef RFPS_CHECKED
     uint32_t n_total;          // points of all clouds (the length of pts4 / porig)
 #endif
@@ -870,7 +874,8 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         if (wpt) wxyz = vxyz;
                         else if (wk != 0ull && lane < static_cast<int>(C) && RFPS_IN(wr < (FAST ? nloc : G)))
                             wxyz = FAST ? v.best[wr] : s_sxyz[wr];
-                        if (lane < static_cast<int>(C)) {
+                        // (counting kernels: a lost round sends nothing, so its waits run out)
+                        if (lane < static_cast<int>(C) && !(COUNTERS && j == a.lost_iter)) {
                             const uint32_t rb = buf ? rbar1 : rbar0;
                             st_async_u64(buf ? rkey1 : rkey0, wk, rb);
                             st_async_f32x4(buf ? rxyz1 : rxyz0, wxyz, rb);
@@ -883,7 +888,8 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                                 if (NREG == 2 && (vis & 2u)) ct1.w = v.ct[my + NT].w;
                             }
                         }
-                        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&s_mbar[buf], ph, kSpinLimit))) {
+                        if (!__all_sync(0xffffffffu,
+                                        mbar_wait_bounded(&s_mbar[buf], ph, COUNTERS ? a.spin_limit : kSpinLimit))) {
                             if (lane == 0) atomicCAS(&a.hdr->status, 0u, kStatusTimeout);
                             s_abort = 1;
                             // the fast path has no CTA barrier per iteration: this warp leaves on its own,
@@ -1140,7 +1146,8 @@ cudaError_t launch_floor(int C, int64_t iters, unsigned long long* sink, cudaStr
 }  // namespace
 
 cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int64_t* out, const rfps_opts& o,
-                          int64_t n_clouds, int64_t max_n, cudaStream_t st, bool save_state)
+                          int64_t n_clouds, int64_t max_n, cudaStream_t st, bool save_state, int64_t lost_iter,
+                          uint32_t spin_limit)
 {
     (void)max_n;
     SampleArgs a;
@@ -1162,12 +1169,14 @@ cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int6
     a.smem_bytes = 0;   // set per instantiation from the device's opt-in limit
     a.resident = 1;
     a.save_state = save_state ? 1 : 0;
+    a.lost_iter = lost_iter;
+    a.spin_limit = spin_limit ? spin_limit : kSpinLimit;
 #ifdef RFPS_CHECKED
     a.n_total = static_cast<uint32_t>(L.total_n);
 #endif
     const int C = o.cluster;
     const bool cl = C > 1;
-    if (o.counters) {
+    if (o.counters || lost_iter != 0) {   // the failure-path test runs in the counting kernels
         return cl ? launch_nt<true, true>(a, o.threads, C, n_clouds, st)
                   : launch_nt<false, true>(a, o.threads, C, n_clouds, st);
     }

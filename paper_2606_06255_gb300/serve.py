@@ -23,6 +23,22 @@ next (so one bad request cannot take its batch-mates down), and a request
 that fails on its own is retried up to `max_retries` times, then reported
 as failed.  A request may carry a queueing deadline (dropped as expired if
 not admitted in time) and a cancellation time (dropped if still queued then).
+
+Kept indices and follow-up requests (incremental sampling, Sec. 3.3-3.4): a
+request with keep=True leaves its cloud's voxel index and FPS state (every
+point's distance, the records' Dist_v keys, the last sample) on the device
+after it is served; a later request with more_of=<that rid> asks for m more
+samples of the same sequence and is served from that state, without the
+points travelling again and without repeating the first samples' work.  A
+kept index counts against the memory budget until a follow-up without
+keep=True consumes it or the run ends.  A follow-up waits while its base
+request is still queued or running, and fails if the base was not kept.
+
+Size-aware routing: an executor may ask for some requests to run alone
+(alone(r) -> True; the GPU executor does so for clouds above `tail_n` points,
+which it launches with their own launch shape, e.g. a cluster of CTAs
+instead of one CTA), so that the few largest clouds, which set the latency
+tail, get more of the GPU each.
 """
 
 from __future__ import annotations
@@ -45,6 +61,8 @@ class Request:
     deadline: float | None = None    # seconds after arrival by which it must be admitted
     cancel_at: float | None = None   # the client withdraws it at this time if still queued
     attempts: int = 0                # launches that failed so far
+    keep: bool = False               # keep the device index and FPS state for follow-ups
+    more_of: int | None = None       # continue the sequence of this earlier (kept) request by m samples
 
 
 @dataclass
@@ -74,6 +92,7 @@ class Report:
     window: tuple = (0.0, 0.0)       # first and last arrival
     max_inflight_batches: int = 0
     peak_mem: int = 0
+    followups: int = 0               # follow-up requests served from a kept index
 
     def summary(self) -> dict:
         lat = sorted(c.latency for c in self.completed)
@@ -99,6 +118,7 @@ class Report:
             "mean_batch_size": statistics.mean(c.batch_size for c in self.completed) if n else None,
             "max_inflight_batches": self.max_inflight_batches,
             "peak_device_bytes": self.peak_mem,
+            "followups_served": self.followups,
             "samples_per_s": sum(c.samples for c in self.completed) / self.makespan if self.makespan else None,
         }
 
@@ -117,6 +137,7 @@ def merge_reports(reports) -> "Report":
         out.cancelled += r.cancelled
         out.max_inflight_batches = max(out.max_inflight_batches, r.max_inflight_batches)
         out.peak_mem += r.peak_mem
+        out.followups += r.followups
     if live:
         t0 = min(r.window[0] for r in live)
         t1 = max(r.window[1] for r in live)
@@ -154,18 +175,38 @@ class Server:
         mem_used = 0
         last_finish = 0.0
         alone = set()            # rids that run in a batch of their own after a batch failure
+        kept = {}                # rid -> device bytes of its kept index
+        busy = set()             # kept rids a follow-up is running on
+        settled = set()          # rids that completed or were dropped (a follow-up of one not kept fails)
+        ex_alone = getattr(self.ex, "alone", None)
+
+        def runs_alone(r):
+            return r.keep or r.more_of is not None or r.rid in alone or bool(ex_alone and ex_alone(r))
+
+        def release(rid):
+            nonlocal mem_used
+            if rid in kept:
+                mem_used -= kept.pop(rid)
+                self.ex.release(rid)
 
         def requeue(batch, reason):
             # a failed micro-batch: its requests go back to the head of the queue to run alone; one
-            # that failed alone spends a retry, and fails for good when they run out
+            # that failed alone spends a retry, and fails for good when they run out.  A follow-up
+            # is not retried: the kept state it started from is no longer trusted.
             for r in reversed(batch):
                 if len(batch) > 1:
                     alone.add(r.rid)
                     queue.appendleft(r)
                     continue
                 r.attempts += 1
-                if r.attempts > self.max_retries:
+                if r.more_of is not None:
+                    busy.discard(r.more_of)
+                    release(r.more_of)
                     rep.failed.append((r.rid, reason))
+                    settled.add(r.rid)
+                elif r.attempts > self.max_retries:
+                    rep.failed.append((r.rid, reason))
+                    settled.add(r.rid)
                 else:
                     queue.appendleft(r)
 
@@ -181,8 +222,10 @@ class Server:
                 for r in queue:
                     if r.cancel_at is not None and now >= r.cancel_at:
                         rep.cancelled.append(r.rid)
+                        settled.add(r.rid)
                     elif r.deadline is not None and now > r.arrival + r.deadline:
                         rep.expired.append(r.rid)
+                        settled.add(r.rid)
                     else:
                         keep.append(r)
                 progressed = progressed or len(keep) != len(queue)
@@ -196,28 +239,61 @@ class Server:
                     except Exception as e:   # a device error reported with the results
                         results = None
                         requeue(batch, f"results: {e}")
+                    mem_used -= mem
                     if results is not None:
                         for r, idx in zip(batch, results):
                             rep.completed.append(Completed(r.rid, r.arrival, t_adm, t_done, len(batch), idx, len(idx)))
+                            settled.add(r.rid)
+                            if r.more_of is not None:      # the kept state moved on to this request
+                                rep.followups += 1
+                                busy.discard(r.more_of)
+                                held = kept.pop(r.more_of, 0)
+                                if r.keep:
+                                    kept[r.rid] = held
+                                else:
+                                    mem_used -= held
+                                    self.ex.release(r.rid)
+                            elif r.keep:
+                                kept[r.rid] = self.ex.kept_bytes(r.rid)
+                                mem_used += kept[r.rid]
                         last_finish = max(last_finish, t_done)
-                    mem_used -= mem
                     free_slots.append(slot)
                     del inflight[slot]
                     progressed = True
             while queue and free_slots:
+                # a follow-up whose base is still queued or running waits; one whose base was not
+                # kept (finished without keep, failed, dropped) fails now
+                blocked = []
+                while queue and queue[0].more_of is not None and (queue[0].more_of not in kept
+                                                                   or queue[0].more_of in busy):
+                    r = queue.popleft()
+                    if r.more_of in settled and r.more_of not in kept:
+                        rep.failed.append((r.rid, "follow-up of a request whose index was not kept"))
+                        settled.add(r.rid)
+                        progressed = True
+                    else:
+                        blocked.append(r)
+                if not queue:
+                    queue.extendleft(reversed(blocked))
+                    break
                 head = queue[0]
                 if self.ex.mem_needed([head]) > self.budget:
                     rep.rejected.append(queue.popleft().rid)     # can never fit
+                    settled.add(head.rid)
+                    queue.extendleft(reversed(blocked))
                     progressed = True
                     continue
                 batch = []
                 while queue and len(batch) < self.max_batch:
-                    if batch and (queue[0].rid in alone or batch[0].rid in alone):
+                    if batch and (runs_alone(queue[0]) or runs_alone(batch[0])):
+                        break
+                    if batch and queue[0].more_of is not None:
                         break
                     need = self.ex.mem_needed(batch + [queue[0]])
                     if mem_used + need > self.budget:
                         break
                     batch.append(queue.popleft())
+                queue.extendleft(reversed(blocked))
                 if not batch:
                     break                                        # wait for memory to free up
                 need = self.ex.mem_needed(batch)
@@ -230,6 +306,8 @@ class Server:
                     progressed = True
                     break
                 inflight[slot] = (handle, batch, clock() - t0, need)
+                if batch[0].more_of is not None:
+                    busy.add(batch[0].more_of)
                 mem_used += need
                 rep.peak_mem = max(rep.peak_mem, mem_used)
                 rep.max_inflight_batches = max(rep.max_inflight_batches, len(inflight))
@@ -239,6 +317,8 @@ class Server:
                 if i < len(reqs) and not inflight and not queue:
                     wait = max(0.0, min(reqs[i].arrival - now, 0.01))
                 sleep(wait)
+        for rid in list(kept):       # kept indices live as long as the run
+            release(rid)
         rep.makespan = last_finish - (reqs[0].arrival if reqs else 0.0)
         return rep
 
@@ -253,7 +333,7 @@ class GpuExecutor:
     come back into a pinned buffer.  All of it is ordered on the slot's stream.
     """
 
-    def __init__(self, n_slots: int, opts=None, device=None):
+    def __init__(self, n_slots: int, opts=None, device=None, tail_opts=None, tail_n: int | None = None):
         import ctypes
 
         import torch
@@ -266,18 +346,75 @@ class GpuExecutor:
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(n_slots)]
         self.opts = opts
         self._opts = _lib.Opts(**opts) if opts else None
+        # clouds of tail_n points or more run alone with their own launch shape
+        self.tail_n = tail_n if tail_opts is not None else None
+        self.tail_opts = tail_opts
+        self._tail_opts = _lib.Opts(**tail_opts) if tail_opts else None
+        self.kept = {}        # rid -> Index kept on the device for follow-up requests
+
+    def alone(self, r) -> bool:
+        return self.tail_n is not None and r.more_of is None and r.points.shape[0] >= self.tail_n
+
+    def _route(self, batch):
+        if len(batch) == 1 and self.alone(batch[0]):
+            return self.tail_opts, self._tail_opts
+        return self.opts, self._opts
 
     def mem_needed(self, batch) -> int:
         if not batch:
             return 0
+        if batch[0].more_of is not None:           # the kept index already holds the cloud
+            return 8 * batch[0].m + 4096
+        opts, _ = self._route(batch)
         sizes = [r.points.shape[0] for r in batch]
         total = sum(sizes)
-        ws = self.lib.batch_workspace_size(total, len(batch), max(sizes), self.opts)
+        if batch[0].keep:
+            ws = self.lib.host_workspace_size(total, opts)   # the index's own memory (points included)
+        else:
+            ws = self.lib.batch_workspace_size(total, len(batch), max(sizes), opts)
         return total * 12 + ws + 8 * sum(r.m for r in batch) + 4096
+
+    def kept_bytes(self, rid) -> int:
+        ix = self.kept.get(rid)
+        return ix.nbytes if ix is not None else 0
+
+    def release(self, rid):
+        ix = self.kept.pop(rid, None)
+        if ix is not None:
+            ix.free()
+
+    def _launch_kept(self, r, s):
+        """keep=True: build the cloud's index on the device and take the first m samples from it;
+        more_of: the next m samples from the kept index of an earlier request."""
+        torch = self.torch
+        with torch.cuda.stream(s):
+            held = []
+            if r.more_of is not None:
+                ix = self.kept[r.more_of]
+                out = ix.sample_more(r.m, stream=s)
+            else:
+                src = r.points
+                if not isinstance(src, torch.Tensor):
+                    src = torch.from_numpy(np.ascontiguousarray(src, dtype=np.float32)).pin_memory()
+                pts = src.to(self.device, non_blocking=True)
+                ix = self.lib.Index(pts, opts=self.opts, stream=s)   # copies the points on the stream
+                out = ix.sample(r.m, r.start, stream=s)
+                held = [src, pts]
+            host_out = torch.empty(r.m, dtype=torch.int64, pin_memory=True)
+            host_out.copy_(out, non_blocking=True)
+            host_st = torch.empty(1, dtype=torch.int32, pin_memory=True)
+            ix.status_into(host_st, stream=s)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        return {"event": ev, "host_out": host_out, "host_st": host_st, "ooff": np.array([0, r.m]),
+                "index": ix, "rid": r.rid, "base": r.more_of, "keep": (out, *held)}
 
     def launch(self, batch, slot):
         torch = self.torch
         s = self.streams[slot]
+        if len(batch) == 1 and (batch[0].keep or batch[0].more_of is not None):
+            return self._launch_kept(batch[0], s)
+        opts, c_opts = self._route(batch)
         b = len(batch)
         sizes = [int(r.points.shape[0]) for r in batch]
         ms = [int(r.m) for r in batch]
@@ -301,13 +438,13 @@ class GpuExecutor:
                 pts[o:o + src.shape[0]].copy_(src, non_blocking=True)
                 o += src.shape[0]
             dmeta = meta.to(self.device, non_blocking=True)
-            ws = torch.empty(self.lib.batch_workspace_size(total, b, max(sizes), self.opts), dtype=torch.uint8,
+            ws = torch.empty(self.lib.batch_workspace_size(total, b, max(sizes), opts), dtype=torch.uint8,
                              device=self.device)
             out = torch.empty(mtotal, dtype=torch.int64, device=self.device)
             base = dmeta.data_ptr()
             self.lib._check(self.lib.lib().rfps_fps_batched(
                 pts.data_ptr(), total, base, b, base + 8 * (b + 1), base + 16 * (b + 1), max(sizes),
-                out.data_ptr(), self.ctypes.byref(self._opts) if self._opts is not None else None,
+                out.data_ptr(), self.ctypes.byref(c_opts) if c_opts is not None else None,
                 ws.data_ptr(), ws.numel(), s.cuda_stream), "rfps_fps_batched")
             host_out = torch.empty(mtotal, dtype=torch.int64, pin_memory=True)
             host_out.copy_(out, non_blocking=True)
@@ -328,7 +465,13 @@ class GpuExecutor:
     def results(self, handle):
         st = int(handle["host_st"][0])   # copied back with the indices; the event has fired
         if st != 0:
+            if "index" in handle and handle["base"] is None:
+                handle["index"].free()   # a new index that failed is not kept
             raise RuntimeError(f"device status {st}")
+        if "index" in handle:            # the index (new, or moved on by a follow-up) is kept under this rid
+            if handle["base"] is not None:
+                self.kept.pop(handle["base"], None)
+            self.kept[handle["rid"]] = handle["index"]
         o, ooff = handle["host_out"].numpy(), handle["ooff"]
         return [o[ooff[b]:ooff[b + 1]].copy() for b in range(len(ooff) - 1)]
 

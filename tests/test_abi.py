@@ -106,3 +106,13 @@ def test_argument_errors_need_no_device(lib):
 
 def test_launch_counter_starts_at_zero_without_gpu(lib):
     assert lib.rfps_launch_count() >= 0
+
+
+def test_noalloc_capacity_is_pinned(lib):
+    """rfps_fps_noalloc's fixed 64 MiB scratch holds a 725,440-point cloud with default options and
+    not one point more; beyond it the call is rejected on the host (nothing is launched)."""
+    cap = 64 << 20
+    assert lib.rfps_fps_workspace_size(725440, None) <= cap < lib.rfps_fps_workspace_size(725441, None)
+    ENOMEM = 3
+    fake = ctypes.c_void_p(256)
+    assert lib.rfps_fps_noalloc(fake, 725441, 10, 0, fake, None, None) == ENOMEM

@@ -3,8 +3,9 @@
 Sizes are those of the benchmark configurations: the room-like cloud
 (N = 100,000, M = 25,000), the accumulated LiDAR scan (N = 1,124,730,
 M = 16,384), and the ragged 64-cloud batch (M = N/4 each), through the
-library defaults and through every launch shape the benchmark's autotuner
-can pick (so the timed configuration is always one checked here).
+library defaults and through every launch shape and voxel resolution the
+benchmark's autotuner can pick (so the timed configuration is always one
+checked here).
 """
 
 import numpy as np
@@ -23,21 +24,40 @@ def rf():
     return rf
 
 
-# launch shapes the single-cloud benchmark's autotuner chooses between (bench.py TUNE_CANDIDATES)
-BENCH_SHAPES = [{"cluster": 16, "threads": 256}, {"cluster": 16, "threads": 128}, {"cluster": 8, "threads": 256},
-                {"cluster": 16, "threads": 256, "chunk": 256}]
+EUNSUPPORTED = 6   # rfps_status RFPS_EUNSUPPORTED
 
 
-@pytest.mark.parametrize("name", ["room100k", "lidar1m"])
+def tuner_space():
+    """Every option set the single-cloud autotuner (which the benchmark uses) can return: each
+    launch shape of its first stage at every automatic-resolution scale of its second."""
+    from paper_2606_06255_gb300 import autotune
+    return [o if sc == 70 else dict(o, nvox_scale=sc)
+            for o in autotune.default_candidates(False) for sc in autotune.NVOX_SCALES]
+
+
+@pytest.mark.parametrize("name", ["uniform4k", "room100k", "lidar1m"])
 def test_single_cloud_full_size(rf, name):
     (cloud,), _ = cloudgen.workload(name)
     ref = oracle.fps(cloud.points, cloud.m, cloud.start, threads=0)
     d = torch.from_numpy(cloud.points).cuda()
     got = rf.fps(d, cloud.m, cloud.start, check=True).cpu().numpy()
     np.testing.assert_array_equal(got, ref)
-    for o in BENCH_SHAPES:
-        got = rf.fps(d, cloud.m, cloud.start, opts=o, check=True).cpu().numpy()
-        np.testing.assert_array_equal(got, ref, err_msg=str(o))
+    out = torch.empty(cloud.m, dtype=torch.int64, device="cuda")
+    ran = 0
+    for o in tuner_space():
+        ws = torch.empty(rf.workspace_size(d.shape[0], o), dtype=torch.uint8, device="cuda")
+        out.fill_(-1)
+        rf.fps(d, cloud.m, cloud.start, opts=o, workspace=ws, out=out)
+        st = rf.status(ws)
+        # a single CTA indexes at most ~150k records; finer grids on one or two CTAs report that
+        # (and the autotuner drops such a candidate); every other option set samples exactly
+        assert st in (0, EUNSUPPORTED), (o, st)
+        if st == 0:
+            ran += 1
+            np.testing.assert_array_equal(out.cpu().numpy(), ref, err_msg=str(o))
+        else:
+            assert o.get("cluster", 16) <= 2 and o.get("nvox_scale", 70) > 70, o
+    assert ran >= len(tuner_space()) * 3 // 4
     # the best plain baseline on the same cloud
     variant = 2 if cloud.points.shape[0] > 200000 else 1
     plain = rf.plain_fps(d, cloud.m, cloud.start, variant=variant).cpu().numpy()

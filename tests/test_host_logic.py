@@ -40,15 +40,44 @@ class SimExecutor:
 
     def launch(self, batch, slot):
         self.launched.append([r.rid for r in batch])
-        res = [oracle.fps(r.points, r.m, r.start) for r in batch]
+        res = []
+        for r in batch:
+            if r.more_of is not None:     # continue the kept sequence: the slice of a longer run
+                pts, start, taken = self.kept[r.more_of]
+                res.append(oracle.fps(pts, taken + r.m, start)[taken:])
+            else:
+                res.append(oracle.fps(r.points, r.m, r.start))
         dur = max(r.m for r in batch) * self.per_sample
-        return {"t_done": self.clock() + dur, "res": res}
+        return {"t_done": self.clock() + dur, "res": res, "batch": batch}
 
     def done(self, h):
         return self.clock() >= h["t_done"]
 
     def results(self, h):
+        for r in h["batch"]:
+            if r.more_of is not None:
+                pts, start, taken = self.kept.pop(r.more_of)
+                self.kept[r.rid] = (pts, start, taken + r.m)
+            elif r.keep:
+                self.kept[r.rid] = (r.points, r.start, r.m)
         return h["res"]
+
+    # kept indices (follow-up requests)
+    kept_size = 10_000
+
+    @property
+    def kept(self):
+        if not hasattr(self, "_kept"):
+            self._kept = {}
+            self.released = []
+        return self._kept
+
+    def kept_bytes(self, rid):
+        return self.kept_size if rid in self.kept else 0
+
+    def release(self, rid):
+        self.kept.pop(rid, None)
+        self.released.append(rid)
 
 
 def _requests(n, rate, seed=0):
@@ -209,9 +238,18 @@ def test_two_ranks_over_gloo_shard_without_collectives_on_data():
 
 
 def test_full_size_parity_covers_every_shape_the_bench_can_time():
+    """The benchmark takes its launch shape and resolution from the library's two-stage autotuner;
+    the full-size parity test runs every option set that tuner can return, and the space the bench
+    line states is the tuner's."""
     import bench
     import test_gpu_fullsize
-    assert bench.TUNE_CANDIDATES == test_gpu_fullsize.BENCH_SHAPES
+    from paper_2606_06255_gb300 import autotune
+    assert bench.TUNER_SPACE == autotune.candidate_space(False)
+    space = test_gpu_fullsize.tuner_space()
+    for o in autotune.default_candidates(False):
+        assert o in space
+        for sc in autotune.NVOX_SCALES:
+            assert (o if sc == 70 else dict(o, nvox_scale=sc)) in space
 
 
 def test_reports_of_sharded_servers_merge_into_the_whole_stream():
@@ -267,3 +305,78 @@ def test_clock_sampler_counts_only_the_timed_region_and_falls_back_to_adjacent_r
     cs.lines = [(now - 3.0, _smi_line(500)), (now - 0.05, _smi_line(2060)), (now + 60.0, _smi_line(2070))]
     r = cs.stop()
     assert r["window"] == "adjacent" and r["samples"] == 2 and r["sm_mhz"] == 2065.0
+
+
+def test_followups_continue_kept_sequences_exactly():
+    """keep=True leaves a request's FPS state on the device; follow-ups (more_of) continue the
+    same sequence: base + follow-ups equal one FPS run of the total M.  A follow-up that arrives
+    while its base is still running waits for it; one of a request that was not kept fails; two
+    follow-ups of the same state cannot both run (the second finds it moved on and fails)."""
+    clk = FakeClock()
+    ex = SimExecutor(clk, per_sample_s=1e-5)
+    a = cloudgen.uniform_cloud(1500, seed=31)
+    b = cloudgen.uniform_cloud(900, seed=32)
+    reqs = [
+        serve.Request(0, 0.0, a, 100, 7, keep=True),
+        serve.Request(1, 0.0001, a, 50, 0, keep=True, more_of=0),   # arrives while 0 runs: waits
+        serve.Request(2, 0.05, a, 25, 0, more_of=1),                 # the chain's last step: released
+        serve.Request(3, 0.0, b, 40, 0),                             # not kept
+        serve.Request(4, 0.05, b, 10, 0, more_of=3),                 # fails: nothing kept
+        serve.Request(5, 0.0, b, 60, 2, keep=True),
+        serve.Request(6, 0.06, b, 20, 0, more_of=5),
+        serve.Request(7, 0.06, b, 20, 0, more_of=5),                 # same state as 6: fails
+    ]
+    rep = serve.Server(ex, mem_budget=10**7, max_inflight=4, max_batch=4).run(reqs, clock=clk, sleep=clk.sleep)
+    by_id = {c.rid: c.indices for c in rep.completed}
+    full_a = oracle.fps(a, 175, 7)
+    np.testing.assert_array_equal(by_id[0], full_a[:100])
+    np.testing.assert_array_equal(by_id[1], full_a[100:150])
+    np.testing.assert_array_equal(by_id[2], full_a[150:175])
+    np.testing.assert_array_equal(by_id[6], oracle.fps(b, 80, 2)[60:])
+    assert sorted(rid for rid, _ in rep.failed) == [4, 7]
+    assert rep.followups == 3
+    # every kept state was released (consumed by a follow-up or at the end of the run)
+    assert not ex.kept and sorted(ex.released) == [2, 6]
+    assert [r for r in ex.launched if len(r) > 1 and {0, 1, 2, 5, 6} & set(r)] == []   # kept work runs alone
+
+
+def test_followup_memory_is_held_until_released():
+    """A kept index holds its bytes against the budget between its request and the follow-up."""
+    clk = FakeClock()
+    ex = SimExecutor(clk, bytes_per_point=1)
+    ex.kept_size = 900_000
+    a = cloudgen.uniform_cloud(1000, seed=33)
+    others = [serve.Request(10 + i, 0.001 + 1e-4 * i, cloudgen.uniform_cloud(500, seed=40 + i), 50, 0)
+              for i in range(6)]
+    reqs = [serve.Request(0, 0.0, a, 100, 0, keep=True), serve.Request(1, 0.5, a, 100, 0, more_of=0)] + others
+    rep = serve.Server(ex, mem_budget=1_000_000, max_inflight=4, max_batch=2).run(reqs, clock=clk, sleep=clk.sleep)
+    assert len(rep.completed) == 8 and not rep.failed
+    assert rep.peak_mem <= 1_000_000
+    assert rep.peak_mem >= 900_000      # the kept index was counted while the others ran
+
+
+class RoutingExecutor(SimExecutor):
+    """Clouds of `tail_n` points or more run alone (as the GPU executor's size-aware route)."""
+
+    def __init__(self, clock, tail_n, **kw):
+        super().__init__(clock, **kw)
+        self.tail_n = tail_n
+
+    def alone(self, r):
+        return r.points.shape[0] >= self.tail_n
+
+
+def test_size_aware_routing_runs_large_clouds_alone():
+    clk = FakeClock()
+    ex = RoutingExecutor(clk, tail_n=1500)
+    reqs = _requests(30, rate=5000.0, seed=8)
+    rep = serve.Server(ex, mem_budget=10**8, max_inflight=4, max_batch=8).run(reqs, clock=clk, sleep=clk.sleep)
+    assert len(rep.completed) == 30
+    big = {r.rid for r in reqs if r.points.shape[0] >= 1500}
+    assert big
+    for b in ex.launched:
+        if set(b) & big:
+            assert len(b) == 1
+    by_id = {c.rid: c.indices for c in rep.completed}
+    for r in reqs:
+        np.testing.assert_array_equal(by_id[r.rid], oracle.fps(r.points, r.m, r.start))

@@ -46,9 +46,40 @@ def test_noalloc_matches_rfps_fps_twice():
         out = torch.full((m,), -1, dtype=torch.int64, device="cuda")
         rc = lib.rfps_fps_noalloc(pts.data_ptr(), pts.shape[0], m, start, out.data_ptr(), None, s)
         assert rc == 0, rc
-        torch.cuda.synchronize()
+        assert lib.rfps_noalloc_status_read(s) == 0     # no device-side error either
         ref = _reference(lib, pts, m, start)
         np.testing.assert_array_equal(out.cpu().numpy(), ref)
+
+
+def test_noalloc_non_default_options():
+    """Other options change the scratch layout; the result is still rfps_fps's."""
+    from paper_2606_06255_gb300 import Opts
+    lib = _lib()
+    s = torch.cuda.current_stream().cuda_stream
+    pts = torch.from_numpy(cloudgen.room_cloud(30000, seed=43)).cuda()
+    m = 4000
+    o = Opts(threads=128, chunk=256, cluster=4)
+    out = torch.full((m,), -1, dtype=torch.int64, device="cuda")
+    assert lib.rfps_fps_noalloc(pts.data_ptr(), pts.shape[0], m, 5, out.data_ptr(), ctypes.byref(o), s) == 0
+    assert lib.rfps_noalloc_status_read(s) == 0
+    np.testing.assert_array_equal(out.cpu().numpy(), _reference(lib, pts, m, 5))
+
+
+def test_noalloc_reports_device_errors_then_recovers():
+    """A non-finite coordinate is only visible on the device: the call returns 0 and the status read
+    reports it; the next call on good points starts from a clean status word."""
+    lib = _lib()
+    s = torch.cuda.current_stream().cuda_stream
+    bad = cloudgen.room_cloud(5000, seed=44)
+    bad[1234, 1] = np.nan
+    pts = torch.from_numpy(bad).cuda()
+    out = torch.empty(100, dtype=torch.int64, device="cuda")
+    assert lib.rfps_fps_noalloc(pts.data_ptr(), pts.shape[0], 100, 0, out.data_ptr(), None, s) == 0
+    assert lib.rfps_noalloc_status_read(s) == 2      # RFPS_ENONFINITE
+    good = torch.from_numpy(cloudgen.room_cloud(5000, seed=45)).cuda()
+    assert lib.rfps_fps_noalloc(good.data_ptr(), good.shape[0], 100, 0, out.data_ptr(), None, s) == 0
+    assert lib.rfps_noalloc_status_read(s) == 0
+    np.testing.assert_array_equal(out.cpu().numpy(), _reference(lib, good, 100, 0))
 
 
 def test_noalloc_rejects_beyond_capacity():
