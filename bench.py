@@ -454,15 +454,23 @@ def measure_batch64(args, rf, torch, world=1, rank=0):
             "batched_vs_plain_batched": min(p["ms"] for p in plain.values()) / t_batch}
 
 
-def measure_serving(args, rf, world=1, rank=0):
+# size-aware route of the serving run: clouds of TAIL_N points or more (the latency tail) run
+# alone on a cluster of CTAs instead of one CTA each
+TAIL_N = 600_000
+TAIL_OPTS = {"cluster": 4, "threads": 256}
+
+
+def measure_serving(args, rf, world=1, rank=0, routed=False):
     """Poisson request stream through the continuous-batching server.  Under torchrun the stream
     is sharded round-robin over the ranks, each serving its share on its own GPU; rank 0 merges
-    the outcomes (latency percentiles and throughput over the whole stream)."""
+    the outcomes (latency percentiles and throughput over the whole stream).  routed=True adds the
+    size-aware route of the largest clouds."""
     from paper_2606_06255_gb300 import serve
     # throughput setting: one CTA of 512 threads per cloud (the most SM-efficient shape), many streams
     opts = json.loads(args.opts) if args.opts else {"cluster": 1, "threads": 512}
     reqs = serve.poisson_workload(args.requests + 16, args.rate, pinned=True)
-    ex = serve.GpuExecutor(args.slots, opts=opts)
+    ex = serve.GpuExecutor(args.slots, opts=opts, tail_opts=TAIL_OPTS if routed else None,
+                           tail_n=TAIL_N if routed else None)
     srv = serve.Server(ex, mem_budget=48 << 30, max_inflight=args.slots, max_batch=args.max_batch)
     srv.run([r for r in reqs[:16] if r.rid % world == rank])
     t0 = reqs[16].arrival
@@ -484,6 +492,8 @@ def measure_serving(args, rf, world=1, rank=0):
     out.update({"metric": "p99 latency / clouds/s", "workload": "serving", "offered_rate": args.rate,
                 "requests": args.requests, "opts": opts, "slots": args.slots, "max_batch": args.max_batch,
                 "sizes": "N log-uniform [20000, 1200000], M = N/8, half room / half LiDAR"})
+    if routed:
+        out["route"] = {"tail_n": TAIL_N, "tail_opts": TAIL_OPTS}
     return out
 
 
@@ -724,6 +734,8 @@ def main(argv=None):
                 line[name] = measure_batch64(args, rf, torch)
             elif name == "serving":
                 line[name] = measure_serving(args, rf)
+                # the same stream with the largest clouds routed to a 4-CTA cluster each
+                line[name]["routed"] = measure_serving(args, rf, routed=True)
     if line is not None and args.workload in SINGLE and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_subprocess(args.workload)   # after the GPU work, in a clean process
     if line is not None:

@@ -87,14 +87,33 @@ constexpr uint32_t kSpinLimit = 1u << 22;   // try_wait rounds before a wait giv
 // Shared-memory record state of one CTA (fast path): ct = (centre, prune
 // threshold), best = (best point, covering radius), key = Dist_v key, rng =
 // point range; local record l is global record gbase + l * C.
+//
+// When a lane holds more than two records (the loop that reads them from shared memory every
+// iteration), the four arrays are stored warp-major: the record of slot s = l mod NT (lane
+// s / NW of warp s mod NW) sits at pp(l), where the records of one warp are consecutive, so the
+// lanes of a warp reading their own records touch consecutive addresses instead of addresses
+// NW * 16 bytes apart in the same banks.  The last, partial block of NT records is packed the
+// same way.  The register-held paths keep the plain order (at(l) = l): they read the arrays
+// rarely and the index arithmetic would lengthen their critical path (both measured).
+template <int NT>
 struct RecView {
+    static constexpr uint32_t NW = NT / 32;
     float4* ct;
     float4* best;
     unsigned long long* key;
     uint2* rng;
-    uint32_t gbase, C;
+    uint32_t gbase, C, nloc;
+    bool perm;
     const SampleArgs* a;
     __device__ __forceinline__ uint32_t g(uint32_t l) const { return gbase + l * C; }
+    __device__ __forceinline__ uint32_t pp(uint32_t l) const
+    {
+        const uint32_t s = l % NT, base = l - s, w = s % NW, ln = s / NW;
+        const uint32_t rem = min(static_cast<uint32_t>(NT), nloc - base);
+        const uint32_t q = rem / NW, r = rem % NW;
+        return base + w * q + min(w, r) + ln;
+    }
+    __device__ __forceinline__ uint32_t at(uint32_t l) const { return perm ? pp(l) : l; }
 };
 
 struct Cnt {
@@ -322,10 +341,13 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
             // Fast path: every record of this CTA in shared memory (52 bytes each),
             // then as many points as fit (20 bytes each).
             const bool fast = static_cast<size_t>(nloc) * 52 + 16 <= a.smem_bytes && nloc <= 32u * NT;
-            RecView v;
+            const int nb = static_cast<int>((nloc + NT - 1) / NT);   // records per lane (fast path)
+            RecView<NT> v;
             v.a = &a;
             v.C = C;
             v.gbase = gbase;
+            v.nloc = nloc;
+            v.perm = fast && !(NT <= 256 && nb <= 2);   // the iteration loop of MODE 3 below
             float4* s_pts = nullptr;
             uint32_t* s_orig = nullptr;
             uint32_t* s_soff = nullptr;
@@ -338,7 +360,13 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
             float4* s_sxyz = nullptr;            // best point of the super, radius in .w
             unsigned long long* s_skey = nullptr;
             uint32_t* s_slist = nullptr;         // unpruned super-records of this iteration
-            uint32_t* s_rlist = nullptr;         // unpruned records of this iteration
+            uint2* s_sent = nullptr;             // per super-record: its range in the record list
+            // record list (unpruned records of this iteration): local record, point range, and
+            // the new key and best point its visit produced
+            uint32_t* s_rlist = nullptr;
+            uint2* s_rrng = nullptr;
+            unsigned long long* s_rkey = nullptr;
+            float4* s_rxyz = nullptr;
             uint32_t G = 0, W = 0;
             if (fast) {
                 v.ct = reinterpret_cast<float4*>(smem);
@@ -359,15 +387,15 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     const float4 sph = a.rec_sph[k];
                     const uint2 rg = a.rec_rng[k];
                     if (resume) {   // saved state: threshold, best point (radius in .w), key
-                        v.ct[l] = make_float4(sph.x, sph.y, sph.z, a.rec_thr[k]);
-                        v.best[l] = a.rec_best[k];
-                        v.key[l] = a.rec_key[k];
+                        v.ct[v.at(l)] = make_float4(sph.x, sph.y, sph.z, a.rec_thr[k]);
+                        v.best[v.at(l)] = a.rec_best[k];
+                        v.key[v.at(l)] = a.rec_key[k];
                     } else {
-                        v.ct[l] = make_float4(sph.x, sph.y, sph.z, nan);
-                        v.best[l] = make_float4(0.f, 0.f, 0.f, sph.w);
-                        v.key[l] = 0ull;
+                        v.ct[v.at(l)] = make_float4(sph.x, sph.y, sph.z, nan);
+                        v.best[v.at(l)] = make_float4(0.f, 0.f, 0.f, sph.w);
+                        v.key[v.at(l)] = 0ull;
                     }
-                    v.rng[l] = rg;
+                    v.rng[v.at(l)] = rg;
                     mine += rg.y;
                 }
                 (void)mine;
@@ -379,17 +407,17 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     const uint32_t per = (nloc + NT - 1) / NT;
                     const uint32_t l0 = min(nloc, t * per), l1 = min(nloc, l0 + per);
                     uint32_t sum = 0;
-                    for (uint32_t l = l0; l < l1; ++l) sum += v.rng[l].y;
+                    for (uint32_t l = l0; l < l1; ++l) sum += v.rng[v.at(l)].y;
                     uint32_t total;
                     uint32_t off = block_exclusive_sum<NT>(sum, s_scr, &total);
                     for (uint32_t l = l0; l < l1; ++l) {
-                        const uint32_t cnt = v.rng[l].y;
+                        const uint32_t cnt = v.rng[v.at(l)].y;
                         s_soff[l] = (off + cnt <= P) ? off : 0xffffffffu;   // shared-memory offset, or not resident
                         off += cnt;
                     }
                     __syncthreads();
                     for (uint32_t l = w; l < nloc; l += NW) {
-                        const uint2 rg = v.rng[l];
+                        const uint2 rg = v.rng[v.at(l)];
                         const uint32_t so = s_soff[l];
                         if (so == 0xffffffffu) continue;
                         for (uint32_t q = lane; q < rg.y; q += 32) {
@@ -399,7 +427,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     }
                     __syncthreads();
                     for (uint32_t l = t; l < nloc; l += NT)
-                        if (s_soff[l] != 0xffffffffu) v.rng[l].x = kResident | s_soff[l];
+                        if (s_soff[l] != 0xffffffffu) v.rng[v.at(l)].x = kResident | s_soff[l];
                     resident = true;
                 }
             } else {
@@ -408,20 +436,25 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                 // records' spheres, the max of their Dist_v keys and the coordinates of the point
                 // that attains it, kept in shared memory.  Pruning tests super-records first.
                 G = (nloc + 31) / 32;
-                if (static_cast<size_t>(G) * 44 + 16 > a.smem_bytes) {
-                    // more records than one CTA can index (beyond ~150k per CTA): larger clusters
+                if (static_cast<size_t>(G) * 52 + 16 > a.smem_bytes) {
+                    // more records than one CTA can index (beyond ~140k per CTA): larger clusters
                     // or records are needed; record the error and skip the cloud uniformly
                     if (t == 0) atomicCAS(&a.hdr->status, 0u, kStatusUnsupported);
                     G = 0;
                 }
+                // 52 bytes per super-record (16-byte arrays first), then 36 per record-list entry
                 s_sct = reinterpret_cast<float4*>(smem);
                 s_sxyz = s_sct + G;
                 s_skey = reinterpret_cast<unsigned long long*>(s_sxyz + G);
-                s_slist = reinterpret_cast<uint32_t*>(s_skey + G);
-                s_rlist = s_slist + G;
-                const size_t used = static_cast<size_t>(G) * 44;
-                const size_t room = a.smem_bytes > used ? (a.smem_bytes - used) / 4 : 0;
+                s_sent = reinterpret_cast<uint2*>(s_skey + G);
+                s_slist = reinterpret_cast<uint32_t*>(s_sent + G);
+                const size_t used = (static_cast<size_t>(G) * 52 + 15) & ~static_cast<size_t>(15);
+                const size_t room = a.smem_bytes > used ? (a.smem_bytes - used) / 36 : 0;
                 W = static_cast<uint32_t>(room < nloc ? room : nloc);
+                s_rxyz = reinterpret_cast<float4*>(smem + used);
+                s_rkey = reinterpret_cast<unsigned long long*>(s_rxyz + W);
+                s_rrng = reinterpret_cast<uint2*>(s_rkey + W);
+                s_rlist = reinterpret_cast<uint32_t*>(s_rrng + W);
                 if (!resume) {
                     for (uint32_t l = t; l < nloc; l += NT) {
                         const uint32_t k = v.g(l);
@@ -500,21 +533,25 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
             // MODE 0 hierarchical; 1 and 2 fast with this lane's one or two records' centres and
             // thresholds held in registers (nloc <= NT, <= 2 NT; 128- and 256-thread CTAs, whose
             // register budget has room for it); 3 fast with any number per lane.
-            const int nb = static_cast<int>((nloc + NT - 1) / NT);
             auto iterate = [&](auto mode) {
                 constexpr int MODE = decltype(mode)::value;
                 constexpr bool FAST = MODE != 0;
                 constexpr int NREG = MODE == 1 || MODE == 2 ? MODE : 0;
+                // position of record l in the shared-memory arrays (warp-major in MODE 3)
+                auto Q = [&](uint32_t l) -> uint32_t {
+                    if constexpr (MODE == 3) return v.pp(l);
+                    else return l;
+                };
                 float4 ct0 = make_float4(0.f, 0.f, 0.f, 0.f), ct1 = ct0;
                 // counting runs: the shadow check of a pruned record held by this CTA
                 auto shadow_record = [&](uint32_t l) -> uint64_t {
-                    const uint2 rg = v.rng[l];
+                    const uint2 rg = v.rng[Q(l)];
                     return (resident && (rg.x & kResident)) ? shadow_pruned(s_pts, rg.x & ~kResident, rg.y, sx, sy, sz)
                                                             : shadow_pruned(a.pts4, rg.x, rg.y, sx, sy, sz);
                 };
                 if constexpr (NREG > 0) {
-                    if (my < nloc) ct0 = v.ct[my];
-                    if (NREG == 2 && my + NT < nloc) ct1 = v.ct[my + NT];
+                    if (my < nloc) ct0 = v.ct[Q(my)];
+                    if (NREG == 2 && my + NT < nloc) ct1 = v.ct[Q(my + NT)];
                 }
                 for (int64_t j = 1; j < c.m; ++j) {
                     const bool first = (j == 1) && !resume;   // the initial update of Sec. 3.3
@@ -535,10 +572,10 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         const float wy = __shfl_sync(0xffffffffu, by, rl);
                         const float wz = __shfl_sync(0xffffffffu, bz, rl);
                         if (lane == 0) {
-                            const float r = v.best[l].w;
-                            v.key[l] = rk;
-                            v.best[l] = make_float4(wx, wy, wz, r);
-                            v.ct[l].w = prune_threshold(r, rk);
+                            const float r = v.best[Q(l)].w;
+                            v.key[Q(l)] = rk;
+                            v.best[Q(l)] = make_float4(wx, wy, wz, r);
+                            v.ct[Q(l)].w = prune_threshold(r, rk);
                         }
                     };
                     if constexpr (FAST) {
@@ -559,7 +596,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             for (int b = 0; b < nb; ++b) {
                                 const uint32_t l = static_cast<uint32_t>(b) * NT + my;
                                 if (l < nloc) {
-                                    const bool keep = first || !a.prune || !prune_by_threshold(v.ct[l], sx, sy, sz);
+                                    const bool keep = first || !a.prune || !prune_by_threshold(v.ct[Q(l)], sx, sy, sz);
                                     um |= keep ? (1u << b) : 0u;
                                     if (COUNTERS && !first) {
                                         ++cn.tests;
@@ -577,7 +614,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             for (int b = 0; b < (NREG > 0 ? NREG : nb); ++b) {
                                 const uint32_t l = static_cast<uint32_t>(b) * NT + my;
                                 if (l < nloc && !((um >> b) & 1u)) {
-                                    const unsigned long long kk = v.key[l];
+                                    const unsigned long long kk = v.key[Q(l)];
                                     if (kk > lkey) {
                                         lkey = kk;
                                         lrec = l;
@@ -603,7 +640,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             const uint32_t l = static_cast<uint32_t>(__ffs(mm) - 1) * NT + static_cast<uint32_t>(src * NW + w);
                             if (lane == src) rem &= rem - 1u;
                             if (!RFPS_IN(l < nloc)) continue;
-                            const uint2 rg = v.rng[l];
+                            const uint2 rg = v.rng[Q(l)];
                             float bx = 0.f, by = 0.f, bz = 0.f;
                             const bool in_smem = resident && (rg.x & kResident);
 #ifdef RFPS_CHECKED
@@ -644,10 +681,10 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                                 const float wy = __shfl_sync(0xffffffffu, by, rl);
                                 const float wz = __shfl_sync(0xffffffffu, bz, rl);
                                 if (lane == 0) {
-                                    const float r = v.best[l].w;
-                                    v.key[l] = rk;
-                                    v.best[l] = make_float4(wx, wy, wz, r);
-                                    v.ct[l].w = prune_threshold(r, rk);
+                                    const float r = v.best[Q(l)].w;
+                                    v.key[Q(l)] = rk;
+                                    v.best[Q(l)] = make_float4(wx, wy, wz, r);
+                                    v.ct[Q(l)].w = prune_threshold(r, rk);
                                     if (rk > pk) {
                                         pk = rk;
                                         prec = l;
@@ -656,25 +693,26 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             }
                         }
                     } else {
-                        // one warp updates record l (global memory) and refreshes its key, best point
-                        // and prune threshold
-                        auto visit_global = [&](uint32_t l) {
+                        // one warp updates record l (global memory; point range rg, covering radius r):
+                        // its points' distances, then its key, best point and prune threshold in global
+                        // memory.  The new key and best point are returned to every lane.
+                        auto visit_global = [&](uint32_t l, uint2 rg, float r, unsigned long long& rk, float& wx,
+                                                float& wy, float& wz) {
+                            rk = 0ull;
+                            wx = wy = wz = 0.f;
                             if (!RFPS_IN(l < nloc)) return;
                             const uint32_t k = v.g(l);
-                            const uint2 rg = a.rec_rng[k];
 #ifdef RFPS_CHECKED
                             if (!RFPS_IN(static_cast<uint64_t>(rg.x) + rg.y <= a.n_total)) return;
 #endif
                             float bx = 0.f, by = 0.f, bz = 0.f;
                             const unsigned long long lk = visit_points<PPL, COUNTERS>(
                                 a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx, sy, sz, lane, bx, by, bz, cn);
-                            unsigned long long rk;
                             const int wl = warp_argmax_lane(lk, &rk);
-                            const float wx = __shfl_sync(0xffffffffu, bx, wl);
-                            const float wy = __shfl_sync(0xffffffffu, by, wl);
-                            const float wz = __shfl_sync(0xffffffffu, bz, wl);
+                            wx = __shfl_sync(0xffffffffu, bx, wl);
+                            wy = __shfl_sync(0xffffffffu, by, wl);
+                            wz = __shfl_sync(0xffffffffu, bz, wl);
                             if (lane == 0) {
-                                const float r = a.rec_best[k].w;
                                 a.rec_key[k] = rk;
                                 a.rec_best[k] = make_float4(wx, wy, wz, r);
                                 a.rec_thr[k] = prune_threshold(r, rk);
@@ -724,72 +762,117 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             s_rlcut[par ^ 1] = W;
                         }
                         const uint32_t nsl = s_wlc[par];
-                        // ---- A2: records of the unpruned super-records (one per lane); unpruned ones
-                        // go to the record list, or are visited in place when the list is full
+                        // ---- A2: records of the unpruned super-records (one per lane).  Each record's
+                        // sphere, threshold, point range, key and best point come in one round of
+                        // loads; unpruned records go to the record list with their range and radius (or
+                        // are visited in place when the list is full).  The max key over the others,
+                        // which this iteration leaves unchanged, and its point go into the super-record's
+                        // key and best point (read by nothing before the refresh in C rewrites them).
                         for (uint32_t i = w; i < nsl; i += NW) {
                             const uint32_t g = s_slist[i];
                             if (!RFPS_IN(g < G)) continue;
                             const uint32_t l = g * 32 + lane;
                             bool keep = false;
-                            if (l < nloc) {
-                                if (first || !a.prune) {
-                                    keep = true;
-                                } else {
-                                    const uint32_t k = v.g(l);
-                                    const float4 sp = a.rec_sph[k];
-                                    keep = !prune_by_threshold(make_float4(sp.x, sp.y, sp.z, a.rec_thr[k]), sx, sy, sz);
-                                }
-                                if (COUNTERS && !first) {
-                                    ++cn.tests;
-                                    cn.pruned += keep ? 0 : 1;
-                                    if (!keep && a.prune) {
-                                        const uint2 rg = a.rec_rng[v.g(l)];
-                                        cn.pviol += shadow_pruned(a.pts4, rg.x, rg.y, sx, sy, sz);
-                                    }
-                                }
-                            }
-                            uint32_t mask = __ballot_sync(0xffffffffu, keep);
-                            if (!mask) continue;
-                            uint32_t base = 0;
-                            if (lane == 0) base = atomicAdd(&s_rlc[par], static_cast<uint32_t>(__popc(mask)));
-                            base = __shfl_sync(0xffffffffu, base, 0);
-                            if (base + __popc(mask) <= W) {
-                                if (keep) s_rlist[base + __popc(mask & ((1u << lane) - 1u))] = l;
-                            } else {
-                                // list full: later appends fail too, so the list holds [0, first failed base)
-                                if (lane == 0) atomicMin(&s_rlcut[par], base);
-                                while (mask) {
-                                    const int src = __ffs(mask) - 1;
-                                    mask &= mask - 1;
-                                    visit_global(g * 32 + static_cast<uint32_t>(src));
-                                }
-                            }
-                        }
-                        __syncthreads();
-                        // ---- B: one warp per listed record
-                        const uint32_t nrl = min(min(s_rlc[par], s_rlcut[par]), W);
-                        for (uint32_t i = w; i < nrl; i += NW) visit_global(s_rlist[i]);
-                        __syncthreads();
-                        // ---- C: refresh the unpruned super-records from their records
-                        for (uint32_t i = w; i < nsl; i += NW) {
-                            const uint32_t g = s_slist[i];
-                            if (!RFPS_IN(g < G)) continue;
-                            const uint32_t l = g * 32 + lane;
+                            uint2 rg = make_uint2(0u, 0u);
                             unsigned long long kk = 0ull;
                             float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
                             if (l < nloc) {
-                                kk = a.rec_key[v.g(l)];
-                                b4 = a.rec_best[v.g(l)];
+                                const uint32_t k = v.g(l);
+                                const float4 sp = a.rec_sph[k];
+                                const float thr = a.rec_thr[k];
+                                rg = a.rec_rng[k];
+                                kk = a.rec_key[k];
+                                b4 = a.rec_best[k];
+                                keep = first || !a.prune || !prune_by_threshold(make_float4(sp.x, sp.y, sp.z, thr), sx, sy, sz);
+                                if (COUNTERS && !first) {
+                                    ++cn.tests;
+                                    cn.pruned += keep ? 0 : 1;
+                                    if (!keep && a.prune) cn.pviol += shadow_pruned(a.pts4, rg.x, rg.y, sx, sy, sz);
+                                }
+                            }
+                            unsigned long long pmk;
+                            const int pl = warp_argmax_lane(keep ? 0ull : kk, &pmk);
+                            float px4 = __shfl_sync(0xffffffffu, b4.x, pl);
+                            float py4 = __shfl_sync(0xffffffffu, b4.y, pl);
+                            float pz4 = __shfl_sync(0xffffffffu, b4.z, pl);
+                            uint32_t mask = __ballot_sync(0xffffffffu, keep);
+                            uint2 ent = make_uint2(0u, 0u);
+                            if (mask) {
+                                uint32_t base = 0;
+                                if (lane == 0) base = atomicAdd(&s_rlc[par], static_cast<uint32_t>(__popc(mask)));
+                                base = __shfl_sync(0xffffffffu, base, 0);
+                                if (base + __popc(mask) <= W) {
+                                    if (keep) {
+                                        const uint32_t e = base + __popc(mask & ((1u << lane) - 1u));
+                                        s_rlist[e] = l;
+                                        s_rrng[e] = rg;
+                                        s_rxyz[e] = make_float4(0.f, 0.f, 0.f, b4.w);
+                                    }
+                                    ent = make_uint2(base, static_cast<uint32_t>(__popc(mask)));
+                                } else {
+                                    // list full: later appends fail too, so the list holds [0, first failed base)
+                                    if (lane == 0) atomicMin(&s_rlcut[par], base);
+                                    while (mask) {
+                                        const int src = __ffs(mask) - 1;
+                                        mask &= mask - 1;
+                                        const uint2 rs = make_uint2(__shfl_sync(0xffffffffu, rg.x, src),
+                                                                    __shfl_sync(0xffffffffu, rg.y, src));
+                                        const float rr = __shfl_sync(0xffffffffu, b4.w, src);
+                                        unsigned long long rk;
+                                        float wx, wy, wz;
+                                        visit_global(g * 32 + static_cast<uint32_t>(src), rs, rr, rk, wx, wy, wz);
+                                        if (rk > pmk) {
+                                            pmk = rk;
+                                            px4 = wx;
+                                            py4 = wy;
+                                            pz4 = wz;
+                                        }
+                                    }
+                                }
+                            }
+                            if (lane == 0) {
+                                s_skey[g] = pmk;
+                                s_sxyz[g] = make_float4(px4, py4, pz4, s_sxyz[g].w);
+                                s_sent[g] = ent;
+                            }
+                        }
+                        __syncthreads();
+                        // ---- B: one warp per listed record; its new key and best point also go to the list
+                        const uint32_t nrl = min(min(s_rlc[par], s_rlcut[par]), W);
+                        for (uint32_t e = w; e < nrl; e += NW) {
+                            const float r = s_rxyz[e].w;
+                            unsigned long long rk;
+                            float wx, wy, wz;
+                            visit_global(s_rlist[e], s_rrng[e], r, rk, wx, wy, wz);
+                            if (lane == 0) {
+                                s_rkey[e] = rk;
+                                s_rxyz[e] = make_float4(wx, wy, wz, r);
+                            }
+                        }
+                        __syncthreads();
+                        // ---- C: refresh the unpruned super-records: max of the records left unchanged (A2)
+                        // and of the ones visited (B), from shared memory
+                        for (uint32_t i = w; i < nsl; i += NW) {
+                            const uint32_t g = s_slist[i];
+                            if (!RFPS_IN(g < G)) continue;
+                            const uint2 ent = s_sent[g];
+                            if (!RFPS_IN(ent.x + ent.y <= W)) continue;
+                            unsigned long long kk = 0ull;
+                            float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (static_cast<uint32_t>(lane) < ent.y) {
+                                kk = s_rkey[ent.x + lane];
+                                b4 = s_rxyz[ent.x + lane];
                             }
                             unsigned long long gk;
                             const int gl = warp_argmax_lane(kk, &gk);
-                            const float bx = __shfl_sync(0xffffffffu, b4.x, gl);
-                            const float by = __shfl_sync(0xffffffffu, b4.y, gl);
-                            const float bz = __shfl_sync(0xffffffffu, b4.z, gl);
                             if (lane == 0) {
-                                const float srad = s_sxyz[g].w;
+                                const unsigned long long pmk = s_skey[g];   // unchanged records (A2)
+                                float4 bx = s_sxyz[g];
+                                const float srad = bx.w;
+                                if (gk > pmk) bx = s_rxyz[ent.x + gl];
+                                else gk = pmk;
                                 s_skey[g] = gk;
-                                s_sxyz[g] = make_float4(bx, by, bz, srad);
+                                s_sxyz[g] = make_float4(bx.x, bx.y, bx.z, srad);
                                 s_sct[g].w = prune_threshold(srad, gk);
                             }
                         }
@@ -819,7 +902,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         oy = py;
                         oz = pz;
                         if (!ppt && prec != 0xffffffffu && RFPS_IN(prec < nloc)) {
-                            const float4 b4 = v.best[prec];
+                            const float4 b4 = v.best[Q(prec)];
                             ox = b4.x;
                             oy = b4.y;
                             oz = b4.z;
@@ -851,11 +934,11 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         if (lane == 0) {
                             s_wkey[par][w] = wk;
                             s_wxyz[par][w] = wk != 0ull && RFPS_IN(wr < (FAST ? nloc : G))
-                                                 ? (FAST ? v.best[wr] : s_sxyz[wr]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                                                 ? (FAST ? v.best[Q(wr)] : s_sxyz[wr]) : make_float4(0.f, 0.f, 0.f, 0.f);
                         }
                         if constexpr (NREG > 0) {   // thresholds rewritten by this iteration's visits
-                            if (vis & 1u) ct0.w = v.ct[my].w;
-                            if (NREG == 2 && (vis & 2u)) ct1.w = v.ct[my + NT].w;
+                            if (vis & 1u) ct0.w = v.ct[Q(my)].w;
+                            if (NREG == 2 && (vis & 2u)) ct1.w = v.ct[Q(my + NT)].w;
                         }
                         __syncthreads();
                         const unsigned long long ck = lane < NW ? s_wkey[par][lane] : 0ull;
@@ -873,7 +956,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         float4 wxyz = make_float4(0.f, 0.f, 0.f, 0.f);
                         if (wpt) wxyz = vxyz;
                         else if (wk != 0ull && lane < static_cast<int>(C) && RFPS_IN(wr < (FAST ? nloc : G)))
-                            wxyz = FAST ? v.best[wr] : s_sxyz[wr];
+                            wxyz = FAST ? v.best[Q(wr)] : s_sxyz[wr];
                         // (counting kernels: a lost round sends nothing, so its waits run out)
                         if (lane < static_cast<int>(C) && !(COUNTERS && j == a.lost_iter)) {
                             const uint32_t rb = buf ? rbar1 : rbar0;
@@ -884,8 +967,8 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             if (dl != 0xffffffffu) finish_record(dl, dk, dx, dy, dz);
                             __syncwarp();
                             if constexpr (NREG > 0) {   // thresholds rewritten by this iteration's visits
-                                if (vis & 1u) ct0.w = v.ct[my].w;
-                                if (NREG == 2 && (vis & 2u)) ct1.w = v.ct[my + NT].w;
+                                if (vis & 1u) ct0.w = v.ct[Q(my)].w;
+                                if (NREG == 2 && (vis & 2u)) ct1.w = v.ct[Q(my + NT)].w;
                             }
                         }
                         if (!__all_sync(0xffffffffu,
@@ -946,13 +1029,13 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                 if (fast) {
                     for (uint32_t l = t; l < nloc; l += NT) {
                         const uint32_t k = v.g(l);
-                        a.rec_key[k] = v.key[l];
-                        a.rec_best[k] = v.best[l];
-                        a.rec_thr[k] = v.ct[l].w;
+                        a.rec_key[k] = v.key[v.at(l)];
+                        a.rec_best[k] = v.best[v.at(l)];
+                        a.rec_thr[k] = v.ct[v.at(l)].w;
                     }
                     if (resident) {
                         for (uint32_t l = w; l < nloc; l += NW) {
-                            const uint2 rg = v.rng[l];
+                            const uint2 rg = v.rng[v.at(l)];
                             if (!(rg.x & kResident)) continue;
                             const uint32_t go = a.rec_rng[v.g(l)].x, so = rg.x & ~kResident;
                             for (uint32_t q = lane; q < rg.y; q += 32) a.pts4[go + q].w = s_pts[so + q].w;
