@@ -455,9 +455,9 @@ def measure_batch64(args, rf, torch, world=1, rank=0):
 
 
 # size-aware route of the serving run: clouds of TAIL_N points or more (the latency tail) run
-# alone on a cluster of CTAs instead of one CTA each
+# alone on an 8-CTA cluster instead of one CTA each
 TAIL_N = 600_000
-TAIL_OPTS = {"cluster": 4, "threads": 256}
+TAIL_OPTS = {"cluster": 8, "threads": 256}
 
 
 def measure_serving(args, rf, world=1, rank=0, routed=False):
