@@ -65,14 +65,24 @@ def test_single_cloud_full_size(rf, name):
 
 
 def test_batch64_full_size(rf):
+    """The 64-cloud batch through the library defaults and through every option set the batch
+    autotuner (which the benchmark's batch64 run uses) can return."""
     clouds, _ = cloudgen.workload("batch64")
     sizes = [c.points.shape[0] for c in clouds]
     ms = [c.m for c in clouds]
     cat = torch.from_numpy(np.concatenate([c.points for c in clouds])).cuda()
-    refs = [oracle.fps(c.points, c.m, 0, threads=0) for c in clouds]
-    # library defaults and the batch autotuner's pick on this batch (clusters of 8 x 256 threads)
-    for o in (None, {"cluster": 8, "threads": 256, "chunk": 128}):
-        out, ooff = rf.fps_batched(cat, sizes, ms, [0] * len(clouds), opts=o)
-        out = out.cpu().numpy()
-        for b, c in enumerate(clouds):
-            np.testing.assert_array_equal(out[ooff[b]:ooff[b + 1]], refs[b], err_msg=f"cloud {b} (N={sizes[b]}), {o}")
+    refs = np.concatenate([oracle.fps(c.points, c.m, 0, threads=0) for c in clouds])
+    from paper_2606_06255_gb300 import autotune
+    space = [None] + [o if sc == 70 else dict(o, nvox_scale=sc)
+                      for o in autotune.default_candidates(True) for sc in autotune.NVOX_SCALES]
+    meta = rf._lib._batch_meta(sizes, ms, None, cat.device)
+    for o in space:
+        ws = torch.empty(rf.batch_workspace_size(cat.shape[0], len(sizes), max(sizes), o), dtype=torch.uint8,
+                         device="cuda")
+        out, _ = rf.fps_batched(cat, sizes, ms, opts=o, workspace=ws, meta=meta)
+        assert rf.status(ws) == 0, o
+        got = out.cpu().numpy()
+        if not np.array_equal(got, refs):
+            ooff = np.concatenate([[0], np.cumsum(ms)])
+            bad = [b for b in range(len(sizes)) if not np.array_equal(got[ooff[b]:ooff[b + 1]], refs[ooff[b]:ooff[b + 1]])]
+            raise AssertionError(f"{o}: clouds {bad[:5]} differ from the oracle")

@@ -109,6 +109,7 @@ def test_serving_launch_shape_at_full_size(rf):
     ms = [n // 8 for n in sizes]
     starts = [0, 17, 3, 49_999]
     cat = torch.from_numpy(np.concatenate(clouds)).cuda()
+    refs = [oracle.fps(c, ms[b], starts[b], threads=0) for b, c in enumerate(clouds)]
     opts = {"cluster": 1, "threads": 512}
     ws = torch.empty(rf.batch_workspace_size(cat.shape[0], len(clouds), max(sizes), opts), dtype=torch.uint8,
                      device="cuda")
@@ -116,8 +117,14 @@ def test_serving_launch_shape_at_full_size(rf):
     assert rf.status(ws) == 0
     out = out.cpu().numpy()
     for b, c in enumerate(clouds):
-        np.testing.assert_array_equal(out[ooff[b]:ooff[b + 1]], oracle.fps(c, ms[b], starts[b], threads=0),
-                                      err_msg=f"cloud {b} (N={sizes[b]})")
+        np.testing.assert_array_equal(out[ooff[b]:ooff[b + 1]], refs[b], err_msg=f"cloud {b} (N={sizes[b]})")
+    # the serving benchmark's size-aware route: each large cloud alone on an 8-CTA cluster
+    import bench
+    for b in range(2):
+        got = rf.fps_batched(torch.from_numpy(clouds[b]).cuda(), [sizes[b]], [ms[b]], [starts[b]],
+                             opts=bench.TAIL_OPTS)[0].cpu().numpy()
+        np.testing.assert_array_equal(got, refs[b], err_msg=f"routed cloud {b} (N={sizes[b]}), {bench.TAIL_OPTS}")
+    assert sizes[0] >= bench.TAIL_N and sizes[1] >= bench.TAIL_N
 
 
 def test_followups_on_kept_indices_and_tail_routing(rf):

@@ -380,3 +380,25 @@ def test_size_aware_routing_runs_large_clouds_alone():
     by_id = {c.rid: c.indices for c in rep.completed}
     for r in reqs:
         np.testing.assert_array_equal(by_id[r.rid], oracle.fps(r.points, r.m, r.start))
+
+
+def test_bench_arms_print_the_same_config(capsys):
+    """The reference arm (the CPU oracle) prints the same config dict as the GPU arm, which takes it
+    from the same function, so the driver can pair the two lines."""
+    import json
+
+    import bench
+    args = bench.parse(["--impl", "reference", "--workload", "uniform4k", "--steps", "1", "--warmup", "1"])
+    assert bench.run_reference(args, 0) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "samples/s"
+    assert line["config"] == bench.workload_config("uniform4k")[1]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_cpu_baseline_reports_the_three_oracle_timings():
+    import bench
+    c = bench.cpu_timing("uniform4k", budget_s=0.2)
+    assert c["kind"] == "oracle" and c["value"] > 0 and c["cores"] >= 1
+    assert c["plain_1thread"]["cores"] == 1 and c["plain_1thread"]["value"] > 0
+    assert c["radiusfps_1thread"]["n_vox"] == 32 and c["radiusfps_1thread"]["value"] > 0
