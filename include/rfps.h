@@ -63,7 +63,11 @@ typedef enum {
 typedef struct {
     int32_t n_vox;       /* voxel bins per axis, n_vox of Sec. 3.2 (v in Sec. 5.6.2); 1..256 */
     int32_t cluster;     /* CTAs working on one cloud (thread-block cluster size): 1,2,4,8,16 */
-    int32_t threads;     /* threads per CTA of the sampling kernel: 128, 256 or 512 */
+    int32_t threads;     /* threads per CTA of the sampling kernel: 128, 256 or 512.  With
+                            cluster 1 and 512 threads, clouds of at most 8,192 points run on
+                            the register-record path: each thread holds up to 16 consecutive
+                            sorted points as one record of its own (radius_mode and chunk
+                            then apply to nothing) */
     int32_t chunk;       /* max points per voxel record (a voxel with more points is split
                             into several records): power of two in 32..4096; default 128 */
     int32_t prune;       /* 1: spherical-voxel radius pruning (Sec. 3.4.2) on */

@@ -1075,6 +1075,196 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
     }
 }
 
+// Register-record sampler for small clouds on one CTA (N <= NT * P): thread t holds the P sorted
+// points [t P, t P + P) of the cloud in registers -- Morton-consecutive, so they are spatial
+// neighbours -- and treats them as one record of its own: covering sphere (centre of their bounding
+// box, radius measured over them as the build does for voxel records), Dist_v key (max point key)
+// with the coordinates of its point, and the FP32-safe prune threshold.  An iteration is the same
+// method as k_sample's (radius pruning of the record, point skip, strict update, Dist_v resync,
+// Sec. 3.3-3.4) without shared-memory records or warp-serial visits: every thread tests its own
+// record and, if it is not pruned, updates its own points; the selection is a warp argmax, one CTA
+// barrier and an argmax over the warps.  On one SM the per-warp cost of the record-visiting
+// loop sets the iteration time of small clouds (every warp runs ~280 instructions an iteration at
+// 4,096 points on 512 threads), which this form avoids.
+template <int NT, int P, bool COUNTERS>
+__global__ void __launch_bounds__(NT, 1) k_sample_regs(const SampleArgs a)
+{
+    constexpr int NW = NT / 32;
+    __shared__ unsigned long long s_wkey[2][NW];
+    __shared__ float4 s_wxyz[2][NW];
+    __shared__ uint32_t s_item;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const float inf = __int_as_float(0x7f800000), nan = __int_as_float(0x7fc00000);
+    Cnt cn;
+    for (;;) {
+        if (t == 0) {
+            uint32_t item = atomicAdd(&a.hdr->work, 1u);
+            if (*static_cast<volatile uint32_t*>(&a.hdr->status) != 0u) item = 0xffffffffu;
+            s_item = item;
+        }
+        __syncthreads();
+        const uint32_t item = s_item;
+        __syncthreads();   // every thread has read s_item before thread 0 may rewrite it
+        if (item >= a.n_clouds) break;
+        const uint32_t cloud = a.order[item];
+        const CloudDev c = a.clouds[cloud];
+        if (c.valid && RFPS_IN(c.n <= static_cast<int64_t>(NT) * P)) {
+            const bool resume = c.resume != 0;
+            // the cloud's points occupy sorted positions [pt_off, pt_off + n)
+            const uint32_t base = static_cast<uint32_t>(c.pt_off);
+            const uint32_t n = static_cast<uint32_t>(c.n);
+            const uint32_t q0 = static_cast<uint32_t>(t) * P;
+            float px[P], py[P], pz[P], pd[P];
+            uint32_t po[P];
+            float lo[3] = {3.4028234e38f, 3.4028234e38f, 3.4028234e38f};
+            float hi[3] = {-3.4028234e38f, -3.4028234e38f, -3.4028234e38f};
+#pragma unroll
+            for (int u = 0; u < P; ++u) {
+                const uint32_t q = q0 + u;
+                px[u] = py[u] = pz[u] = 0.f;
+                pd[u] = 0.f;
+                po[u] = 0u;
+                if (q < n) {
+                    const float4 p4 = a.pts4[base + q];
+                    px[u] = p4.x;
+                    py[u] = p4.y;
+                    pz[u] = p4.z;
+                    pd[u] = resume ? p4.w : inf;   // +inf: the initial update of Sec. 3.3
+                    po[u] = a.porig[base + q];
+                    lo[0] = fminf(lo[0], p4.x);
+                    lo[1] = fminf(lo[1], p4.y);
+                    lo[2] = fminf(lo[2], p4.z);
+                    hi[0] = fmaxf(hi[0], p4.x);
+                    hi[1] = fmaxf(hi[1], p4.y);
+                    hi[2] = fmaxf(hi[2], p4.z);
+                }
+            }
+            const bool has = q0 < n;
+            // covering sphere: any centre, radius r = max(fl(m (1 + 2^-20)), 2^-50) with
+            // m = max over the members of sqrt(fl d2(p, c)) (the voxel records' rule)
+            const float cx = __fmul_rn(__fadd_rn(lo[0], hi[0]), 0.5f);
+            const float cy = __fmul_rn(__fadd_rn(lo[1], hi[1]), 0.5f);
+            const float cz = __fmul_rn(__fadd_rn(lo[2], hi[2]), 0.5f);
+            float m = 0.f;
+#pragma unroll
+            for (int u = 0; u < P; ++u)
+                if (q0 + u < n) m = fmaxf(m, __fsqrt_rn(sq_dist(px[u], py[u], pz[u], cx, cy, cz)));
+            const float rad = fmaxf(__fmul_rn(m, 0x1.00001p0f), 0x1p-50f);
+            // Dist_v key of the record and its point (resume: from the saved distances)
+            unsigned long long key = 0ull;
+            float bx = 0.f, by = 0.f, bz = 0.f;
+            if (resume) {
+#pragma unroll
+                for (int u = 0; u < P; ++u) {
+                    if (q0 + u < n) {
+                        const unsigned long long kk = make_key(pd[u], po[u]);
+                        if (kk > key) {
+                            key = kk;
+                            bx = px[u];
+                            by = py[u];
+                            bz = pz[u];
+                        }
+                    }
+                }
+            }
+            float4 ct = make_float4(cx, cy, cz, resume ? prune_threshold(rad, key) : nan);
+            const int64_t g0 = c.pt_off + c.start;
+            float sx = resume ? c.last[0] : a.pts[3 * g0 + 0];
+            float sy = resume ? c.last[1] : a.pts[3 * g0 + 1];
+            float sz = resume ? c.last[2] : a.pts[3 * g0 + 2];
+            if (t == 0 && !resume) a.out[c.out_off] = c.start;
+            for (int64_t j = 1; j < c.m; ++j) {
+                const bool first = (j == 1) && !resume;
+                const int par = static_cast<int>(j & 1);
+                const bool keep = has && (first || !a.prune || !prune_by_threshold(ct, sx, sy, sz));
+                if (COUNTERS && !first && has) {
+                    ++cn.tests;
+                    if (!keep) {
+                        ++cn.pruned;
+#pragma unroll
+                        for (int u = 0; u < P; ++u)   // shadow check: no pruned point may improve
+                            if (q0 + u < n && sq_dist(px[u], py[u], pz[u], sx, sy, sz) < pd[u]) ++cn.pviol;
+                    }
+                }
+                if (keep) {
+                    key = 0ull;
+#pragma unroll
+                    for (int u = 0; u < P; ++u) {
+                        if (q0 + u < n) {
+                            const float dx = __fsub_rn(px[u], sx);
+                            const float dy = __fsub_rn(py[u], sy);
+                            const float dz = __fsub_rn(pz[u], sz);
+                            const float xx = __fmul_rn(dx, dx), yy = __fmul_rn(dy, dy), zz = __fmul_rn(dz, dz);
+                            if (a.skip && skip_point(xx, yy, zz, pd[u])) {
+                                if (COUNTERS) {
+                                    ++cn.skip;
+                                    if (__fadd_rn(__fadd_rn(xx, yy), zz) < pd[u]) ++cn.sviol;
+                                }
+                            } else {
+                                const float nd = __fadd_rn(__fadd_rn(xx, yy), zz);
+                                if (nd < pd[u]) {
+                                    pd[u] = nd;
+                                    if (COUNTERS) ++cn.upd;
+                                }
+                            }
+                            if (COUNTERS) ++cn.visit;
+                            const unsigned long long kk = make_key(pd[u], po[u]);
+                            if (kk > key) {
+                                key = kk;
+                                bx = px[u];
+                                by = py[u];
+                                bz = pz[u];
+                            }
+                        }
+                    }
+                    ct.w = prune_threshold(rad, key);
+                }
+                // selection: warp argmax, one CTA barrier, argmax over the warps
+                unsigned long long wk;
+                const int wl = warp_argmax_lane(key, &wk);
+                const float wx = __shfl_sync(0xffffffffu, bx, wl);
+                const float wy = __shfl_sync(0xffffffffu, by, wl);
+                const float wz = __shfl_sync(0xffffffffu, bz, wl);
+                if (lane == 0) {
+                    s_wkey[par][w] = wk;
+                    s_wxyz[par][w] = make_float4(wx, wy, wz, 0.f);
+                }
+                __syncthreads();
+                unsigned long long gbest;
+                const int cl = warp_argmax_lane(lane < NW ? s_wkey[par][lane] : 0ull, &gbest);
+                const float4 cxyz = s_wxyz[par][cl];
+                sx = cxyz.x;
+                sy = cxyz.y;
+                sz = cxyz.z;
+                if (t == 0)
+                    a.out[c.out_off + (resume ? j - 1 : j)] = static_cast<int64_t>(key_index(gbest)) - c.pt_off;
+                if (COUNTERS && t == 0) ++cn.iter;
+            }
+            if (a.save_state) {   // the distances and the last sample, for a later resume
+#pragma unroll
+                for (int u = 0; u < P; ++u)
+                    if (q0 + u < n) a.pts4[base + q0 + u].w = pd[u];
+                if (t == 0) {
+                    a.clouds[cloud].last[0] = sx;
+                    a.clouds[cloud].last[1] = sy;
+                    a.clouds[cloud].last[2] = sz;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (COUNTERS) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[0]), cn.tests);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[1]), cn.pruned);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[2]), cn.visit);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[3]), cn.skip);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[4]), cn.upd);
+        if (t == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[5]), cn.iter);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[6]), cn.pviol);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[7]), cn.sviol);
+    }
+}
+
 // The per-iteration synchronisation floor of k_sample: the same selection
 // tail (warp argmax, CTA slots or DSMEM push, one __syncthreads or one
 // barrier.cluster, slot reduction) with no record work.  `sink` receives a
@@ -1200,6 +1390,25 @@ cudaError_t launch_nt(const SampleArgs& args, int NT, int C, int64_t n_clouds, c
                      : launch_one<512, CLUSTER, COUNTERS>(args, C, n_clouds, st);
 }
 
+// Clouds of at most kRegsNT * P points on one CTA with records held in registers (k_sample_regs).
+constexpr int kRegsNT = 512;
+
+template <int P, bool COUNTERS>
+cudaError_t launch_regs(const SampleArgs& args, int64_t n_clouds, cudaStream_t st)
+{
+    auto kern = k_sample_regs<kRegsNT, P, COUNTERS>;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRegsNT, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int64_t cap = static_cast<int64_t>(per_sm) * sms;
+    kern<<<static_cast<unsigned>(n_clouds < cap ? n_clouds : cap), kRegsNT, 0, st>>>(args);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 template <int NT, bool CLUSTER>
 cudaError_t launch_floor(int C, int64_t iters, unsigned long long* sink, cudaStream_t st)
 {
@@ -1232,7 +1441,6 @@ cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int6
                           int64_t n_clouds, int64_t max_n, cudaStream_t st, bool save_state, int64_t lost_iter,
                           uint32_t spin_limit)
 {
-    (void)max_n;
     SampleArgs a;
     a.hdr = reinterpret_cast<WsHeader*>(ws + L.header);
     a.clouds = reinterpret_cast<CloudDev*>(ws + L.clouds);
@@ -1259,6 +1467,12 @@ cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int6
 #endif
     const int C = o.cluster;
     const bool cl = C > 1;
+    if (C == 1 && o.threads == kRegsNT && max_n <= static_cast<int64_t>(kRegsNT) * 16) {
+        // small clouds on one 512-thread CTA: every thread's points are a record in its registers
+        if (max_n <= static_cast<int64_t>(kRegsNT) * 8)
+            return o.counters ? launch_regs<8, true>(a, n_clouds, st) : launch_regs<8, false>(a, n_clouds, st);
+        return o.counters ? launch_regs<16, true>(a, n_clouds, st) : launch_regs<16, false>(a, n_clouds, st);
+    }
     if (o.counters || lost_iter != 0) {   // the failure-path test runs in the counting kernels
         return cl ? launch_nt<true, true>(a, o.threads, C, n_clouds, st)
                   : launch_nt<false, true>(a, o.threads, C, n_clouds, st);
