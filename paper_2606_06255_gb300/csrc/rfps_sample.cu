@@ -1150,20 +1150,19 @@ __global__ void __launch_bounds__(NT, 1) k_sample_regs(const SampleArgs a)
             for (int u = 0; u < P; ++u)
                 if (q0 + u < n) m = fmaxf(m, __fsqrt_rn(sq_dist(px[u], py[u], pz[u], cx, cy, cz)));
             const float rad = fmaxf(__fmul_rn(m, 0x1.00001p0f), 0x1p-50f);
-            // Dist_v key of the record and its point (resume: from the saved distances)
+            // Dist_v key of the record and its point, from the distances it starts with (+inf, or the
+            // saved ones); it changes only when a distance does
             unsigned long long key = 0ull;
             float bx = 0.f, by = 0.f, bz = 0.f;
-            if (resume) {
 #pragma unroll
-                for (int u = 0; u < P; ++u) {
-                    if (q0 + u < n) {
-                        const unsigned long long kk = make_key(pd[u], po[u]);
-                        if (kk > key) {
-                            key = kk;
-                            bx = px[u];
-                            by = py[u];
-                            bz = pz[u];
-                        }
+            for (int u = 0; u < P; ++u) {
+                if (q0 + u < n) {
+                    const unsigned long long kk = make_key(pd[u], po[u]);
+                    if (kk > key) {
+                        key = kk;
+                        bx = px[u];
+                        by = py[u];
+                        bz = pz[u];
                     }
                 }
             }
@@ -1187,7 +1186,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample_regs(const SampleArgs a)
                     }
                 }
                 if (keep) {
-                    key = 0ull;
+                    bool changed = false;
 #pragma unroll
                     for (int u = 0; u < P; ++u) {
                         if (q0 + u < n) {
@@ -1204,20 +1203,43 @@ __global__ void __launch_bounds__(NT, 1) k_sample_regs(const SampleArgs a)
                                 const float nd = __fadd_rn(__fadd_rn(xx, yy), zz);
                                 if (nd < pd[u]) {
                                     pd[u] = nd;
+                                    changed = true;
                                     if (COUNTERS) ++cn.upd;
                                 }
                             }
                             if (COUNTERS) ++cn.visit;
-                            const unsigned long long kk = make_key(pd[u], po[u]);
-                            if (kk > key) {
-                                key = kk;
-                                bx = px[u];
-                                by = py[u];
-                                bz = pz[u];
-                            }
                         }
                     }
-                    ct.w = prune_threshold(rad, key);
+                    // the Dist_v key and threshold change only when a distance did
+                    if (changed) {
+                        // max over the points' keys as a pairwise tree (empty slots give key 0)
+                        unsigned long long tk[P];
+                        float tx[P], ty[P], tz[P];
+#pragma unroll
+                        for (int u = 0; u < P; ++u) {
+                            tk[u] = q0 + u < n ? make_key(pd[u], po[u]) : 0ull;
+                            tx[u] = px[u];
+                            ty[u] = py[u];
+                            tz[u] = pz[u];
+                        }
+#pragma unroll
+                        for (int h = 1; h < P; h <<= 1) {
+#pragma unroll
+                            for (int u = 0; u + h < P; u += 2 * h) {
+                                if (tk[u + h] > tk[u]) {
+                                    tk[u] = tk[u + h];
+                                    tx[u] = tx[u + h];
+                                    ty[u] = ty[u + h];
+                                    tz[u] = tz[u + h];
+                                }
+                            }
+                        }
+                        key = tk[0];
+                        bx = tx[0];
+                        by = ty[0];
+                        bz = tz[0];
+                        ct.w = prune_threshold(rad, key);
+                    }
                 }
                 // selection: warp argmax, one CTA barrier, argmax over the warps
                 unsigned long long wk;

@@ -103,3 +103,12 @@ def test_ragged_batch_of_small_clouds(rf):
     out = out.cpu().numpy()
     for b, c in enumerate(clouds):
         np.testing.assert_array_equal(out[ooff[b]:ooff[b + 1]], oracle.fps(c, ms[b], starts[b]), err_msg=f"cloud {b}")
+
+
+@pytest.mark.parametrize("opts", [ONE_CTA, {"cluster": 4, "threads": 128}], ids=["registers", "cluster4"])
+def test_squared_distances_that_overflow(rf, opts):
+    """Coordinates up to 4e19: many FP32 squared distances are +inf, so in the first iteration some
+    distances stay +inf (not a strict decrease) and the record keys must still come from them."""
+    pts = cloudgen.uniform_cloud(3000, seed=317) * np.float32(4e19)
+    got = rf.fps(dev(pts), 1200, 3, opts=opts, check=True).cpu().numpy()
+    np.testing.assert_array_equal(got, oracle.fps(pts, 1200, 3))
