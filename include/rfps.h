@@ -64,8 +64,8 @@ typedef struct {
     int32_t n_vox;       /* voxel bins per axis, n_vox of Sec. 3.2 (v in Sec. 5.6.2); 1..256 */
     int32_t cluster;     /* CTAs working on one cloud (thread-block cluster size): 1,2,4,8,16 */
     int32_t threads;     /* threads per CTA of the sampling kernel: 128, 256 or 512.  With
-                            cluster 1 and 512 threads, clouds of at most 8,192 points run on
-                            the register-record path: each thread holds up to 16 consecutive
+                            cluster 1 and 512 threads, clouds of at most 4,096 points run on
+                            the register-record path: each thread holds up to 8 consecutive
                             sorted points as one record of its own (radius_mode and chunk
                             then apply to nothing) */
     int32_t chunk;       /* max points per voxel record (a voxel with more points is split
@@ -100,10 +100,11 @@ typedef struct {
 void rfps_opts_default(rfps_opts *opts);
 
 /* The options a call on a cloud of n points will use, automatic fields
- * resolved (host only, no device work): threads 256, clusters of 16 CTAs
- * from 2,048 points up (1 below), records of at most 128 points, nvox_scale
- * 70; n_vox stays 0 when automatic because the device picks it per cloud
- * (nvox_scale / 100 * cbrt(N)).  RFPS_EINVAL for invalid options. */
+ * resolved (host only, no device work): up to 4,096 points one CTA of 512
+ * threads (the register-record path), above that clusters of 16 CTAs of 256
+ * threads; records of at most 128 points, nvox_scale 70; n_vox stays 0 when
+ * automatic because the device picks it per cloud (nvox_scale / 100 *
+ * cbrt(N)).  RFPS_EINVAL for invalid options. */
 rfps_status rfps_opts_resolve(int64_t n, const rfps_opts *in, rfps_opts *out);
 
 /* Human-readable name of a status code (static string, never NULL). */

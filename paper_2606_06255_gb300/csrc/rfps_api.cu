@@ -76,11 +76,13 @@ rfps_opts resolve_opts(const rfps_opts* in, int64_t max_n)
     rfps_opts o;
     rfps_opts_default(&o);
     if (in) o = *in;
-    // Defaults from launch-shape sweeps on GB300: the per-iteration cost is the
-    // cluster exchange plus the unpruned records' work, and 16 CTAs of 256
-    // threads were fastest from 4k points up (room, LiDAR and uniform clouds).
-    if (o.threads != 128 && o.threads != 256 && o.threads != 512) o.threads = 256;
-    if (o.cluster <= 0) o.cluster = max_n < 2048 ? 1 : 16;
+    // Defaults from launch-shape sweeps on GB300: up to 4,096 points one CTA of 512
+    // threads, whose threads hold the points as records in registers, is fastest (uniform,
+    // room and LiDAR clouds of 1k-4k points); above, the per-iteration cost is the cluster
+    // exchange plus the unpruned records' work, and 16 CTAs of 256 threads were fastest.
+    const bool small = max_n <= 4096 && (o.cluster <= 1) && (o.threads <= 0 || o.threads == 512);
+    if (o.threads != 128 && o.threads != 256 && o.threads != 512) o.threads = small ? 512 : 256;
+    if (o.cluster <= 0) o.cluster = (small || max_n < 2048) ? 1 : 16;
     if (o.chunk <= 0) o.chunk = 128;
     if (o.nvox_scale <= 0) o.nvox_scale = 70;
     return o;

@@ -1085,7 +1085,8 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
 // record and, if it is not pruned, updates its own points; the selection is a warp argmax, one CTA
 // barrier and an argmax over the warps.  On one SM the per-warp cost of the record-visiting
 // loop sets the iteration time of small clouds (every warp runs ~280 instructions an iteration at
-// 4,096 points on 512 threads), which this form avoids.
+// 4,096 points on 512 threads), which this form avoids.  A record whose distances did not change
+// keeps its key and threshold.
 template <int NT, int P, bool COUNTERS>
 __global__ void __launch_bounds__(NT, 1) k_sample_regs(const SampleArgs a)
 {
@@ -1412,8 +1413,11 @@ cudaError_t launch_nt(const SampleArgs& args, int NT, int C, int64_t n_clouds, c
                      : launch_one<512, CLUSTER, COUNTERS>(args, C, n_clouds, st);
 }
 
-// Clouds of at most kRegsNT * P points on one CTA with records held in registers (k_sample_regs).
+// Clouds of at most kRegsNT * kRegsP points on one CTA with records held in registers
+// (k_sample_regs).  Eight points per thread: with sixteen the per-thread chain of an unpruned
+// record grows and a 16-CTA cluster is faster (6,000-point clouds: 2.2 against 1.8 ms).
 constexpr int kRegsNT = 512;
+constexpr int kRegsP = 8;
 
 template <int P, bool COUNTERS>
 cudaError_t launch_regs(const SampleArgs& args, int64_t n_clouds, cudaStream_t st)
@@ -1489,11 +1493,9 @@ cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int6
 #endif
     const int C = o.cluster;
     const bool cl = C > 1;
-    if (C == 1 && o.threads == kRegsNT && max_n <= static_cast<int64_t>(kRegsNT) * 16) {
+    if (C == 1 && o.threads == kRegsNT && max_n <= static_cast<int64_t>(kRegsNT) * kRegsP) {
         // small clouds on one 512-thread CTA: every thread's points are a record in its registers
-        if (max_n <= static_cast<int64_t>(kRegsNT) * 8)
-            return o.counters ? launch_regs<8, true>(a, n_clouds, st) : launch_regs<8, false>(a, n_clouds, st);
-        return o.counters ? launch_regs<16, true>(a, n_clouds, st) : launch_regs<16, false>(a, n_clouds, st);
+        return o.counters ? launch_regs<kRegsP, true>(a, n_clouds, st) : launch_regs<kRegsP, false>(a, n_clouds, st);
     }
     if (o.counters || lost_iter != 0) {   // the failure-path test runs in the counting kernels
         return cl ? launch_nt<true, true>(a, o.threads, C, n_clouds, st)

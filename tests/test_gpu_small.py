@@ -1,7 +1,8 @@
-"""Small clouds on one 512-thread CTA (N <= 8,192): each thread's points are a record held in
-registers (k_sample_regs).  Element-by-element parity with the oracle over the sizes around the
-two register capacities (8 and 16 points per thread), exact ties, duplicates, prune / skip
-switches, incremental sampling with the distance state, the shadow checks and ragged batches."""
+"""Small clouds on one 512-thread CTA (N <= 4,096): each thread's 8 points are a record held in
+registers (k_sample_regs; the library default for clouds this small).  Element-by-element parity
+with the oracle over the sizes around the capacity (and past it, where the same options run the
+shared-memory loop), exact ties, duplicates, prune / skip switches, incremental sampling with the
+distance state, overflowing distances, the shadow checks and ragged batches."""
 
 import numpy as np
 import pytest
@@ -39,18 +40,19 @@ def test_sizes_around_the_register_capacities(rf, n):
                          ids=lambda o: str(o) or "default")
 def test_structured_clouds_and_switches(rf, kind, opts):
     if kind == "room":
-        pts = cloudgen.room_cloud(6000, seed=310)
+        pts = cloudgen.room_cloud(4000, seed=310)
     elif kind == "lidar":
-        pts = cloudgen.lidar_cloud(7000, seed=311)
+        pts = cloudgen.lidar_cloud(3500, seed=311)
     elif kind == "lattice":          # equal distances everywhere: the smallest index must win
         g = np.meshgrid(np.arange(16), np.arange(16), np.arange(16), indexing="ij")
         pts = np.stack([a.ravel() for a in g], 1).astype(np.float32)
-    elif kind == "duplicates":       # past 2,000 samples every candidate is at distance 0
-        base = cloudgen.uniform_cloud(2000, seed=312)
-        pts = base[np.random.default_rng(313).permutation(np.repeat(np.arange(2000), 3))]
+    elif kind == "duplicates":       # past 1,300 samples every candidate is at distance 0
+        base = cloudgen.uniform_cloud(1300, seed=312)
+        pts = base[np.random.default_rng(313).permutation(np.repeat(np.arange(1300), 3))]
     else:
         pts = np.zeros((3000, 3), np.float32)
         pts[:, 0] = np.arange(3000, dtype=np.float32) * 0.25
+    assert pts.shape[0] <= 4096
     m = min(pts.shape[0], 2500)
     got = rf.fps(dev(pts), m, 5, opts=dict(ONE_CTA, **opts), check=True).cpu().numpy()
     np.testing.assert_array_equal(got, oracle.fps(pts, m, 5, threads=0))
@@ -58,7 +60,8 @@ def test_structured_clouds_and_switches(rf, kind, opts):
 
 def test_uniform4k_workload(rf):
     (c,), _ = cloudgen.workload("uniform4k")
-    for opts in (ONE_CTA, dict(ONE_CTA, nvox_scale=35), dict(ONE_CTA, nvox_scale=140)):
+    assert rf.resolved_opts(4096)["threads"] == 512 and rf.resolved_opts(4096)["cluster"] == 1
+    for opts in (None, ONE_CTA, dict(ONE_CTA, nvox_scale=35), dict(ONE_CTA, nvox_scale=140)):
         got = rf.fps(dev(c.points), c.m, c.start, opts=opts, check=True).cpu().numpy()
         np.testing.assert_array_equal(got, oracle.fps(c.points, c.m, c.start), err_msg=str(opts))
 
@@ -66,7 +69,7 @@ def test_uniform4k_workload(rf):
 def test_incremental_sampling_and_distance_state(rf):
     """Pieces taken through the kept index equal one oracle run of the total M, and after each call
     the distance state (Alg. 1's D) equals the oracle's after the same number of samples, bit for bit."""
-    pts = cloudgen.room_cloud(7500, seed=314)
+    pts = cloudgen.room_cloud(4000, seed=314)
     ref, d2 = oracle.fps(pts, 3000, 9, return_d2=True)
     _, d2_700 = oracle.fps(pts, 700, 9, return_d2=True)
     ix = rf.Index(dev(pts), opts=ONE_CTA)
@@ -79,8 +82,8 @@ def test_incremental_sampling_and_distance_state(rf):
 
 
 def test_shadow_checks_and_counters(rf):
-    pts = cloudgen.room_cloud(8000, seed=315)
-    m = 2000
+    pts = cloudgen.room_cloud(4000, seed=315)
+    m = 1500
     opts = dict(ONE_CTA, counters=1)
     ws = torch.empty(rf.workspace_size(pts.shape[0], opts), dtype=torch.uint8, device="cuda")
     got = rf.fps(dev(pts), m, 0, opts=opts, workspace=ws).cpu().numpy()
@@ -94,7 +97,7 @@ def test_shadow_checks_and_counters(rf):
 
 def test_ragged_batch_of_small_clouds(rf):
     rng = np.random.default_rng(316)
-    sizes = [int(x) for x in rng.integers(1, 8193, size=20)] + [8192, 1, 4096]
+    sizes = [int(x) for x in rng.integers(1, 4097, size=20)] + [4096, 1, 4095]
     clouds = [cloudgen.room_cloud(n, seed=400 + i) if i % 2 else cloudgen.uniform_cloud(n, seed=400 + i)
               for i, n in enumerate(sizes)]
     ms = [max(1, n // 4) for n in sizes]
