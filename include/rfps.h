@@ -65,9 +65,9 @@ typedef struct {
     int32_t cluster;     /* CTAs working on one cloud (thread-block cluster size): 1,2,4,8,16 */
     int32_t threads;     /* threads per CTA of the sampling kernel: 128, 256 or 512.  With
                             cluster 1 and 512 threads, clouds of at most 4,096 points run on
-                            the register-record path: each thread holds up to 8 consecutive
-                            sorted points as one record of its own (radius_mode and chunk
-                            then apply to nothing) */
+                            the register-record path instead: one CTA of 1,024 threads, each
+                            holding up to 4 consecutive sorted points as one record of its own
+                            (radius_mode and chunk then apply to nothing) */
     int32_t chunk;       /* max points per voxel record (a voxel with more points is split
                             into several records): power of two in 32..4096; default 128 */
     int32_t prune;       /* 1: spherical-voxel radius pruning (Sec. 3.4.2) on */
@@ -100,8 +100,8 @@ typedef struct {
 void rfps_opts_default(rfps_opts *opts);
 
 /* The options a call on a cloud of n points will use, automatic fields
- * resolved (host only, no device work): up to 4,096 points one CTA of 512
- * threads (the register-record path), above that clusters of 16 CTAs of 256
+ * resolved (host only, no device work): up to 4,096 points cluster 1 and
+ * threads 512 (the register-record path), above that clusters of 16 CTAs of 256
  * threads; records of at most 128 points, nvox_scale 70; n_vox stays 0 when
  * automatic because the device picks it per cloud (nvox_scale / 100 *
  * cbrt(N)).  RFPS_EINVAL for invalid options. */

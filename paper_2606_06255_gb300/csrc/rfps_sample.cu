@@ -1414,10 +1414,12 @@ cudaError_t launch_nt(const SampleArgs& args, int NT, int C, int64_t n_clouds, c
 }
 
 // Clouds of at most kRegsNT * kRegsP points on one CTA with records held in registers
-// (k_sample_regs).  Eight points per thread: with sixteen the per-thread chain of an unpruned
-// record grows and a 16-CTA cluster is faster (6,000-point clouds: 2.2 against 1.8 ms).
-constexpr int kRegsNT = 512;
-constexpr int kRegsP = 8;
+// (k_sample_regs), chosen by the options cluster 1, threads 512.  Fewer points per thread shorten
+// the chain of an unpruned record: 1,024 threads of 4 points measured 3-5 % faster than 512 of 8
+// on 1k-4k-point clouds, 256 of 16 about 40 % slower, and 512 of 16 (to 8,192 points) lost to a
+// 16-CTA cluster (6,000-point clouds: 2.2 against 1.8 ms).
+constexpr int kRegsNT = 1024;
+constexpr int kRegsP = 4;
 
 template <int P, bool COUNTERS>
 cudaError_t launch_regs(const SampleArgs& args, int64_t n_clouds, cudaStream_t st)
@@ -1493,8 +1495,8 @@ cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int6
 #endif
     const int C = o.cluster;
     const bool cl = C > 1;
-    if (C == 1 && o.threads == kRegsNT && max_n <= static_cast<int64_t>(kRegsNT) * kRegsP) {
-        // small clouds on one 512-thread CTA: every thread's points are a record in its registers
+    if (C == 1 && o.threads == 512 && max_n <= static_cast<int64_t>(kRegsNT) * kRegsP) {
+        // small clouds on one CTA: every thread's points are a record in its registers
         return o.counters ? launch_regs<kRegsP, true>(a, n_clouds, st) : launch_regs<kRegsP, false>(a, n_clouds, st);
     }
     if (o.counters || lost_iter != 0) {   // the failure-path test runs in the counting kernels

@@ -1,4 +1,4 @@
-"""Small clouds on one 512-thread CTA (N <= 4,096): each thread's 8 points are a record held in
+"""Small clouds on one CTA (N <= 4,096; options cluster 1, threads 512): each of 1,024 threads holds up to 4 points as a record in
 registers (k_sample_regs; the library default for clouds this small).  Element-by-element parity
 with the oracle over the sizes around the capacity (and past it, where the same options run the
 shared-memory loop), exact ties, duplicates, prune / skip switches, incremental sampling with the
