@@ -1,8 +1,9 @@
-"""Small clouds on one CTA (N <= 4,096; options cluster 1, threads 512): each of 1,024 threads holds up to 4 points as a record in
-registers (k_sample_regs; the library default for clouds this small).  Element-by-element parity
-with the oracle over the sizes around the capacity (and past it, where the same options run the
-shared-memory loop), exact ties, duplicates, prune / skip switches, incremental sampling with the
-distance state, overflowing distances, the shadow checks and ragged batches."""
+"""Small clouds on one CTA (N <= 4,096; options cluster 1, threads 512): each of 1,024 threads
+holds up to 4 points as a record in registers (k_sample_regs; the library default for clouds this
+small).  Element-by-element parity with the oracle over the sizes around the capacity (and past
+it, where the same options run the shared-memory loop), exact ties, duplicates, prune / skip
+switches, incremental sampling with the distance state, overflowing distances, the shadow checks
+and ragged batches."""
 
 import numpy as np
 import pytest
