@@ -251,13 +251,17 @@ def cpu_timing(name, budget_s=10.0):
     n, m = cloud.points.shape[0], cloud.m
     threads = oracle.openmp_threads() or 1
     reps, secs = time_oracle(cloud, budget_s)
-    m1 = min(m, 2048)
-    t0 = time.perf_counter()
-    oracle.fps(cloud.points, m1, cloud.start, threads=1)
-    t1 = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.radiusfps(cloud.points, m, cloud.start, n_vox=32)
-    t2 = time.perf_counter() - t0
+    m1 = min(m, 1024)
+
+    def median_s(fn, k=3):
+        ts = []
+        for _ in range(k):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        return statistics.median(ts)
+    t1 = median_s(lambda: oracle.fps(cloud.points, m1, cloud.start, threads=1))
+    t2 = median_s(lambda: oracle.radiusfps(cloud.points, m, cloud.start, n_vox=32))
     plain1 = m1 / t1
     return {
         "value": reps * m / secs, "unit": "samples/s", "cores": threads, "kind": "oracle",
@@ -265,10 +269,10 @@ def cpu_timing(name, budget_s=10.0):
                   f"{secs:.1f} s, in a separate process without a CUDA context",
         "placement": placement(),
         "plain_1thread": {"value": plain1, "unit": "samples/s", "cores": 1,
-                          "sample": f"the first {m1} of the {m} samples ({t1:.1f} s; plain FPS costs the same "
-                                    "per sample at every step)"},
+                          "sample": f"the first {m1} of the {m} samples, median of 3 runs ({t1:.2f} s; plain FPS "
+                                    "costs the same per sample at every step)"},
         "radiusfps_1thread": {"value": m / t2, "unit": "samples/s", "cores": 1, "n_vox": 32,
-                              "sample": f"one full run ({t2:.2f} s), CPU RadiusFPS oracle (prune + skip)",
+                              "sample": f"full runs, median of 3 ({t2:.2f} s), CPU RadiusFPS oracle (prune + skip)",
                               "speedup_vs_plain_1thread": (m / t2) / plain1},
     }
 
