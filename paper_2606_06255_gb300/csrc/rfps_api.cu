@@ -253,7 +253,7 @@ rfps_status rfps_fps(const float* points, int64_t n, int64_t m, int64_t start, i
     char* ws = static_cast<char*>(workspace);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = launch_setup(ws, L, nullptr, nullptr, nullptr, 1, n, n, m, start, n, o, st);
-    if (e == cudaSuccess) e = launch_build(ws, L, points, o, n, st);
+    if (e == cudaSuccess && !regs_path(o, n)) e = launch_build(ws, L, points, o, n, st);
     if (e == cudaSuccess) e = launch_sample(ws, L, points, out_idx, o, 1, n, st);
     return from_cuda(e);
 }
@@ -308,7 +308,7 @@ rfps_status rfps_fps_host(const float* host_points, int64_t n, int64_t m, int64_
     int64_t* dout = reinterpret_cast<int64_t*>(ws + L.host_out);
     cudaError_t e = cudaMemcpyAsync(dpts, host_points, static_cast<size_t>(n) * 12, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = launch_setup(ws, L, nullptr, nullptr, nullptr, 1, n, n, m, start, n, o, st);
-    if (e == cudaSuccess) e = launch_build(ws, L, dpts, o, n, st);
+    if (e == cudaSuccess && !regs_path(o, n)) e = launch_build(ws, L, dpts, o, n, st);
     if (e == cudaSuccess) e = launch_sample(ws, L, dpts, dout, o, 1, n, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(host_out, dout, static_cast<size_t>(m) * 8, cudaMemcpyDeviceToHost, st);
@@ -339,7 +339,7 @@ rfps_status rfps_fps_batched(const float* points, int64_t total_n, const int64_t
     char* ws = static_cast<char*>(workspace);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = launch_setup(ws, L, offsets, out_offsets, starts, b, total_n, 0, 0, 0, max_n, o, st);
-    if (e == cudaSuccess) e = launch_build(ws, L, points, o, max_n, st);
+    if (e == cudaSuccess && !regs_path(o, max_n)) e = launch_build(ws, L, points, o, max_n, st);
     if (e == cudaSuccess) e = launch_sample(ws, L, points, out_idx, o, b, max_n, st);
     return from_cuda(e);
 }

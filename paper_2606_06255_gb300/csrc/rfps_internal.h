@@ -78,6 +78,10 @@ cudaError_t launch_build(char* ws, const WsLayout& L, const float* points, const
 cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int64_t* out,
                           const rfps_opts& o, int64_t n_clouds, int64_t max_n, cudaStream_t st,
                           bool save_state = false, int64_t lost_iter = 0, uint32_t spin_limit = 0);
+// True when the options send clouds of at most max_n points to the register-record sampler,
+// which groups the points itself unless a kept index is sampled: the caller then skips the
+// index build (launch_build) for a launch without save_state.
+bool regs_path(const rfps_opts& o, int64_t max_n);
 // Synchronisation floor of the sampling loop (same tail, no record work).
 cudaError_t launch_sync_floor(int C, int NT, int64_t iters, unsigned long long* sink, cudaStream_t st);
 // On-chip bandwidth probe (rfps_probe.cu): kind 0 L2 reads of `buf`, kind 1 shared-memory reads.

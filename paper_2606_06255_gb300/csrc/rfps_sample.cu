@@ -1087,13 +1087,23 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
 // loop sets the iteration time of small clouds (every warp runs ~280 instructions an iteration at
 // 4,096 points on 512 threads), which this form avoids.  A record whose distances did not change
 // keeps its key and threshold.
-template <int NT, int P, bool COUNTERS>
+//
+// FUSED: the kernel groups the cloud itself instead of reading the index build's sorted arrays:
+// it reads the caller's points, checks that they are finite (RFPS_ENONFINITE otherwise), sorts
+// them in shared memory by the Morton code of a 1,024^3 grid over their bounding box (bitonic sort
+// of (code, row) pairs), and hands thread t the sorted points [tP, tP + P).  A call then launches
+// two kernels (the cloud table and this one) instead of the index build's thirty.  Any grouping
+// is correct, since the bound holds for any record sphere that covers its points; the Morton
+// order keeps the records compact.  Not for a kept index, whose state lives in the build's arrays.
+template <int NT, int P, bool COUNTERS, bool FUSED>
 __global__ void __launch_bounds__(NT, 1) k_sample_regs(const SampleArgs a)
 {
     constexpr int NW = NT / 32;
     __shared__ unsigned long long s_wkey[2][NW];
     __shared__ float4 s_wxyz[2][NW];
     __shared__ uint32_t s_item;
+    __shared__ unsigned long long s_sort[FUSED ? NT * P : 1];
+    __shared__ float s_box[6][NW];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const float inf = __int_as_float(0x7f800000), nan = __int_as_float(0x7fc00000);
     Cnt cn;
@@ -1119,19 +1129,105 @@ __global__ void __launch_bounds__(NT, 1) k_sample_regs(const SampleArgs a)
             uint32_t po[P];
             float lo[3] = {3.4028234e38f, 3.4028234e38f, 3.4028234e38f};
             float hi[3] = {-3.4028234e38f, -3.4028234e38f, -3.4028234e38f};
+            bool grouped = true;
+            if constexpr (FUSED) {
+                // bounding box and finiteness of the caller's points
+                const float* src = a.pts + 3 * c.pt_off;
+                float mn[3] = {3.4028234e38f, 3.4028234e38f, 3.4028234e38f};
+                float mx[3] = {-3.4028234e38f, -3.4028234e38f, -3.4028234e38f};
+                int bad = 0;
+                for (uint32_t i = t; i < n; i += NT) {
+#pragma unroll
+                    for (int ax = 0; ax < 3; ++ax) {
+                        const float x = src[3 * static_cast<size_t>(i) + ax];
+                        bad |= !(fabsf(x) <= 3.4028234e38f);
+                        mn[ax] = fminf(mn[ax], x);
+                        mx[ax] = fmaxf(mx[ax], x);
+                    }
+                }
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) {
+                    for (int o = 16; o > 0; o >>= 1) {
+                        mn[ax] = fminf(mn[ax], __shfl_xor_sync(0xffffffffu, mn[ax], o));
+                        mx[ax] = fmaxf(mx[ax], __shfl_xor_sync(0xffffffffu, mx[ax], o));
+                    }
+                    if (lane == 0) {
+                        s_box[ax][w] = mn[ax];
+                        s_box[3 + ax][w] = mx[ax];
+                    }
+                }
+                if (__syncthreads_or(bad)) {
+                    if (t == 0) atomicCAS(&a.hdr->status, 0u, kStatusNonFinite);
+                    grouped = false;
+                } else {
+                    float sc[3];
+#pragma unroll
+                    for (int ax = 0; ax < 3; ++ax) {
+                        for (int k = 0; k < NW; ++k) {
+                            mn[ax] = fminf(mn[ax], s_box[ax][k]);
+                            mx[ax] = fmaxf(mx[ax], s_box[3 + ax][k]);
+                        }
+                        const float e = mx[ax] - mn[ax];
+                        sc[ax] = e > 0.f ? 1023.0f / e : 0.f;
+                    }
+                    // (Morton code << 32 | row) pairs, padded to a power of two with the largest key
+                    const uint32_t np2 = n > 1 ? 1u << (32 - __clz(n - 1)) : 1u;
+                    for (uint32_t i = t; i < np2; i += NT) {
+                        unsigned long long kk = ~0ull;
+                        if (i < n) {
+                            uint32_t cq[3];
+#pragma unroll
+                            for (int ax = 0; ax < 3; ++ax) {
+                                const float f = (src[3 * static_cast<size_t>(i) + ax] - mn[ax]) * sc[ax];
+                                cq[ax] = static_cast<uint32_t>(fminf(1023.f, fmaxf(0.f, f)));
+                            }
+                            kk = (static_cast<unsigned long long>(morton3(cq[0], cq[1], cq[2])) << 32) |
+                                 static_cast<uint32_t>(c.pt_off + i);
+                        }
+                        s_sort[i] = kk;
+                    }
+                    __syncthreads();
+                    for (uint32_t k = 2; k <= np2; k <<= 1) {
+                        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                            for (uint32_t i = t; i < np2; i += NT) {
+                                const uint32_t ixj = i ^ j;
+                                if (ixj > i) {
+                                    const unsigned long long x = s_sort[i], y = s_sort[ixj];
+                                    if ((x > y) == ((i & k) == 0)) {
+                                        s_sort[i] = y;
+                                        s_sort[ixj] = x;
+                                    }
+                                }
+                            }
+                            __syncthreads();
+                        }
+                    }
+                }
+            }
 #pragma unroll
             for (int u = 0; u < P; ++u) {
                 const uint32_t q = q0 + u;
                 px[u] = py[u] = pz[u] = 0.f;
                 pd[u] = 0.f;
                 po[u] = 0u;
-                if (q < n) {
-                    const float4 p4 = a.pts4[base + q];
+                // (a cloud that failed its checks was not sorted: nothing of it is read)
+                if (q < n && grouped) {
+                    float4 p4;
+                    if constexpr (FUSED) {
+                        po[u] = static_cast<uint32_t>(s_sort[q]);   // row of the q-th point in Morton order
+#ifdef RFPS_CHECKED
+                        if (!RFPS_IN(po[u] >= c.pt_off && po[u] < c.pt_off + c.n)) po[u] = static_cast<uint32_t>(c.pt_off);
+#endif
+                        p4 = make_float4(a.pts[3 * static_cast<size_t>(po[u])], a.pts[3 * static_cast<size_t>(po[u]) + 1],
+                                         a.pts[3 * static_cast<size_t>(po[u]) + 2], inf);
+                    } else {
+                        p4 = a.pts4[base + q];
+                        po[u] = a.porig[base + q];
+                    }
                     px[u] = p4.x;
                     py[u] = p4.y;
                     pz[u] = p4.z;
                     pd[u] = resume ? p4.w : inf;   // +inf: the initial update of Sec. 3.3
-                    po[u] = a.porig[base + q];
                     lo[0] = fminf(lo[0], p4.x);
                     lo[1] = fminf(lo[1], p4.y);
                     lo[2] = fminf(lo[2], p4.z);
@@ -1140,7 +1236,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample_regs(const SampleArgs a)
                     hi[2] = fmaxf(hi[2], p4.z);
                 }
             }
-            const bool has = q0 < n;
+            const bool has = q0 < n && grouped;
             // covering sphere: any centre, radius r = max(fl(m (1 + 2^-20)), 2^-50) with
             // m = max over the members of sqrt(fl d2(p, c)) (the voxel records' rule)
             const float cx = __fmul_rn(__fadd_rn(lo[0], hi[0]), 0.5f);
@@ -1173,7 +1269,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample_regs(const SampleArgs a)
             float sy = resume ? c.last[1] : a.pts[3 * g0 + 1];
             float sz = resume ? c.last[2] : a.pts[3 * g0 + 2];
             if (t == 0 && !resume) a.out[c.out_off] = c.start;
-            for (int64_t j = 1; j < c.m; ++j) {
+            for (int64_t j = 1; grouped && j < c.m; ++j) {   // (a cloud that failed its checks: none)
                 const bool first = (j == 1) && !resume;
                 const int par = static_cast<int>(j & 1);
                 const bool keep = has && (first || !a.prune || !prune_by_threshold(ct, sx, sy, sz));
@@ -1421,10 +1517,10 @@ cudaError_t launch_nt(const SampleArgs& args, int NT, int C, int64_t n_clouds, c
 constexpr int kRegsNT = 1024;
 constexpr int kRegsP = 4;
 
-template <int P, bool COUNTERS>
+template <int P, bool COUNTERS, bool FUSED>
 cudaError_t launch_regs(const SampleArgs& args, int64_t n_clouds, cudaStream_t st)
 {
-    auto kern = k_sample_regs<kRegsNT, P, COUNTERS>;
+    auto kern = k_sample_regs<kRegsNT, P, COUNTERS, FUSED>;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1495,9 +1591,14 @@ cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int6
 #endif
     const int C = o.cluster;
     const bool cl = C > 1;
-    if (C == 1 && o.threads == 512 && max_n <= static_cast<int64_t>(kRegsNT) * kRegsP) {
-        // small clouds on one CTA: every thread's points are a record in its registers
-        return o.counters ? launch_regs<kRegsP, true>(a, n_clouds, st) : launch_regs<kRegsP, false>(a, n_clouds, st);
+    if (regs_path(o, max_n)) {
+        // small clouds on one CTA: every thread's points are a record in its registers; without a
+        // kept index the kernel groups the points itself (no index build ran)
+        if (save_state)
+            return o.counters ? launch_regs<kRegsP, true, false>(a, n_clouds, st)
+                              : launch_regs<kRegsP, false, false>(a, n_clouds, st);
+        return o.counters ? launch_regs<kRegsP, true, true>(a, n_clouds, st)
+                          : launch_regs<kRegsP, false, true>(a, n_clouds, st);
     }
     if (o.counters || lost_iter != 0) {   // the failure-path test runs in the counting kernels
         return cl ? launch_nt<true, true>(a, o.threads, C, n_clouds, st)
@@ -1505,6 +1606,11 @@ cudaError_t launch_sample(char* ws, const WsLayout& L, const float* points, int6
     }
     return cl ? launch_nt<true, false>(a, o.threads, C, n_clouds, st)
               : launch_nt<false, false>(a, o.threads, C, n_clouds, st);
+}
+
+bool regs_path(const rfps_opts& o, int64_t max_n)
+{
+    return o.cluster == 1 && o.threads == 512 && max_n <= static_cast<int64_t>(kRegsNT) * kRegsP;
 }
 
 cudaError_t launch_sync_floor(int C, int NT, int64_t iters, unsigned long long* sink, cudaStream_t st)

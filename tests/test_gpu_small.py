@@ -116,3 +116,26 @@ def test_squared_distances_that_overflow(rf, opts):
     pts = cloudgen.uniform_cloud(3000, seed=317) * np.float32(4e19)
     got = rf.fps(dev(pts), 1200, 3, opts=opts, check=True).cpu().numpy()
     np.testing.assert_array_equal(got, oracle.fps(pts, 1200, 3))
+
+
+def test_non_finite_coordinates_are_reported(rf):
+    """The register path groups the points itself (no index build runs), so it also checks them:
+    a NaN or an infinity anywhere gives RFPS_ENONFINITE, alone or in a batch, and the workspace then
+    serves a clean call."""
+    pts = cloudgen.room_cloud(3000, seed=318)
+    for bad_value in (np.nan, np.inf, -np.inf):
+        bad = pts.copy()
+        bad[2999, 2] = bad_value
+        ws = torch.empty(rf.workspace_size(3000, ONE_CTA), dtype=torch.uint8, device="cuda")
+        rf.fps(dev(bad), 500, 0, opts=ONE_CTA, workspace=ws)
+        assert rf.status(ws) == 2
+        got = rf.fps(dev(pts), 500, 0, opts=ONE_CTA, workspace=ws).cpu().numpy()
+        assert rf.status(ws) == 0
+        np.testing.assert_array_equal(got, oracle.fps(pts, 500, 0))
+    clouds = [cloudgen.uniform_cloud(1000 + 10 * i, seed=500 + i) for i in range(5)]
+    clouds[3] = clouds[3].copy()
+    clouds[3][7, 0] = np.nan
+    sizes = [c.shape[0] for c in clouds]
+    ws = torch.empty(rf.batch_workspace_size(sum(sizes), 5, max(sizes), ONE_CTA), dtype=torch.uint8, device="cuda")
+    rf.fps_batched(dev(np.concatenate(clouds)), sizes, [100] * 5, opts=ONE_CTA, workspace=ws)
+    assert rf.status(ws) == 2
