@@ -39,8 +39,10 @@ def _reference(lib, pts, m, start):
 def test_noalloc_matches_rfps_fps_twice():
     lib = _lib()
     s = torch.cuda.current_stream().cuda_stream
+    # the third cloud (at most 4,096 points) takes the one-launch register-record path
     cases = [(cloudgen.room_cloud(60000, seed=41), 15000, 0),
-             (cloudgen.lidar_cloud(25000, seed=42), 6000, 17)]
+             (cloudgen.lidar_cloud(25000, seed=42), 6000, 17),
+             (cloudgen.room_cloud(3000, seed=46), 900, 3)]
     for pts_np, m, start in cases:
         pts = torch.from_numpy(pts_np).cuda()
         out = torch.full((m,), -1, dtype=torch.int64, device="cuda")
@@ -80,6 +82,24 @@ def test_noalloc_reports_device_errors_then_recovers():
     assert lib.rfps_fps_noalloc(good.data_ptr(), good.shape[0], 100, 0, out.data_ptr(), None, s) == 0
     assert lib.rfps_noalloc_status_read(s) == 0
     np.testing.assert_array_equal(out.cpu().numpy(), _reference(lib, good, 100, 0))
+
+
+def test_noalloc_small_cloud_error_then_recovery():
+    """The same on the one-launch path for clouds of at most 4,096 points, whose kernel checks the
+    points itself: the error is reported, and the next call's indices are rfps_fps's."""
+    lib = _lib()
+    s = torch.cuda.current_stream().cuda_stream
+    bad = cloudgen.room_cloud(4000, seed=47)
+    bad[3999, 2] = np.inf
+    pts = torch.from_numpy(bad).cuda()
+    out = torch.empty(500, dtype=torch.int64, device="cuda")
+    assert lib.rfps_fps_noalloc(pts.data_ptr(), pts.shape[0], 500, 0, out.data_ptr(), None, s) == 0
+    assert lib.rfps_noalloc_status_read(s) == 2      # RFPS_ENONFINITE
+    for seed in (48, 49):
+        good = torch.from_numpy(cloudgen.room_cloud(4000, seed=seed)).cuda()
+        assert lib.rfps_fps_noalloc(good.data_ptr(), good.shape[0], 500, 7, out.data_ptr(), None, s) == 0
+        assert lib.rfps_noalloc_status_read(s) == 0
+        np.testing.assert_array_equal(out.cpu().numpy(), _reference(lib, good, 500, 7))
 
 
 def test_noalloc_rejects_beyond_capacity():
