@@ -609,13 +609,17 @@ def measure_single(args, rf, torch, name, world=1, rank=0, local=0, full=True):
         best = min(plain.values(), key=lambda p: p["ms_per_cloud"])
         res["best_plain"] = {"variant": best["variant"], "ms_per_cloud": best["ms_per_cloud"],
                              "radiusfps_speedup": best["radiusfps_speedup"]}
-    if not full:
-        return res
-
-    # ---- algorithmic bytes of one sampling launch, from the work counters (untimed run)
+    # ---- work counters of one sampling launch (untimed counting run): exchange rounds, and the
+    # algorithmic bytes below
     cws = torch.empty(rf.workspace_size(n, dict(opts or {}, counters=1)), dtype=torch.uint8, device=dev)
     rf.fps(pts, m, start, opts=dict(opts or {}, counters=1), workspace=cws, out=out)
     c = rf.counters(cws)
+    spr = (m - 1) / max(1, c["rounds"])   # samples per exchange round
+    res.update({"rounds": c["rounds"], "samples_per_round": spr, "ns_per_round": spr * ns_iter,
+                "latency_frac": floor_ns / (spr * ns_iter)})
+    if not full:
+        return res
+
     resynced = c["voxel_tests"] - c["voxels_pruned"]
     alg_bytes = 32 * c["voxel_tests"] + 16 * c["points_visited"] + 4 * c["points_updated"] + 8 * resynced
     peak, peak_kind = load_peaks()
@@ -656,14 +660,17 @@ def measure_single(args, rf, torch, name, world=1, rank=0, local=0, full=True):
         "launch": {"opts": opts or "default", "n_vox": n_vox, "shape": res["launch_shape"], "autotune": tuned},
         "plain_gpu_fps": plain,
         "best_plain": res.get("best_plain"),
-        # The sampling loop is bound by the per-iteration cluster exchange, not by bandwidth: its
-        # headline efficiency is the exchange floor of its launch shape over the time per iteration.
-        "roofline": {"bound": "latency", "achieved": 1e9 / ns_iter, "peak": 1e9 / floor_ns, "unit": "iterations/s",
-                     "frac": floor_ns / ns_iter, "traffic": ncu_traffic(name, opts),
+        # The sampling loop is bound by its cluster exchange rounds, not by bandwidth: its headline
+        # efficiency is the exchange floor of its launch shape over the time per round.  A round
+        # selects one sample, or two when the runner-up shortcut applies (`samples_per_round`, from
+        # the counting run), so the bound per sample is the floor over the samples per round.
+        "roofline": {"bound": "latency", "achieved": 1e9 / ns_iter, "peak": 1e9 * spr / floor_ns,
+                     "unit": "iterations/s", "frac": floor_ns / (spr * ns_iter), "traffic": ncu_traffic(name, opts),
                      "kernel": "k_sample", "kernel_ms": k_ms,
                      "ns_per_iteration": ns_iter, "sync_floor_ns_per_iteration": floor_ns,
-                     "peak_kind": "per-iteration exchange floor of the same launch shape, measured by rfps_sync_floor "
-                                  "in this run",
+                     "rounds": c["rounds"], "samples_per_round": spr, "ns_per_round": spr * ns_iter,
+                     "peak_kind": "exchange floor per round of the same launch shape (rfps_sync_floor, measured in "
+                                  "this run) over the samples per round",
                      "min_floor_ns_per_iteration": min_floor_ns, "launch_shape": res["launch_shape"],
                      "hbm": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                              "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,

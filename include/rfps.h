@@ -94,6 +94,8 @@ typedef struct {
                                   new sample was below their stored one (0 when the bound is safe) */
     uint64_t skip_violations;  /* shadow check: skipped points whose distance to the new sample was
                                   below their stored one (0 when the skip is exact) */
+    uint64_t rounds;          /* selection rounds (cluster exchanges); a round selects two samples
+                                  when the runner-up shortcut applies, so rounds <= iterations */
 } rfps_counters;
 
 /* Fills *opts with the defaults (all automatic, prune = skip = 1). */

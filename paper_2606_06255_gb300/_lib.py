@@ -49,7 +49,8 @@ class Counters(ctypes.Structure):
     _fields_ = [("voxel_tests", ctypes.c_uint64), ("voxels_pruned", ctypes.c_uint64),
                 ("points_visited", ctypes.c_uint64), ("points_skipped", ctypes.c_uint64),
                 ("points_updated", ctypes.c_uint64), ("iterations", ctypes.c_uint64),
-                ("prune_violations", ctypes.c_uint64), ("skip_violations", ctypes.c_uint64)]
+                ("prune_violations", ctypes.c_uint64), ("skip_violations", ctypes.c_uint64),
+                ("rounds", ctypes.c_uint64)]
 
     def as_dict(self):
         return {f[0]: int(getattr(self, f[0])) for f in self._fields_}

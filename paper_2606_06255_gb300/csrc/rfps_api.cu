@@ -39,7 +39,7 @@ __global__ void k_rearm(WsHeader* hdr, CloudDev* clouds, int64_t m, int64_t star
 {
     hdr->status = 0;
     hdr->work = 0;
-    for (int i = 0; i < 8; ++i) hdr->counters[i] = 0;
+    for (int i = 0; i < 9; ++i) hdr->counters[i] = 0;
     clouds[0].m = m;
     clouds[0].start = start;
     clouds[0].out_off = 0;
@@ -216,7 +216,7 @@ const char* rfps_status_str(int s)
     }
 }
 
-int rfps_version(void) { return 2; }
+int rfps_version(void) { return 3; }
 
 rfps_status rfps_opts_resolve(int64_t n, const rfps_opts* in, rfps_opts* out)
 {
@@ -451,6 +451,7 @@ rfps_status rfps_counters_read(const void* workspace, rfps_counters* out, void* 
     out->iterations = h.counters[5];
     out->prune_violations = h.counters[6];
     out->skip_violations = h.counters[7];
+    out->rounds = h.counters[8];
     return RFPS_OK;
 }
 

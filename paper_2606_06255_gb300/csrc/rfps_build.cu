@@ -46,7 +46,7 @@ __global__ void k_setup(WsHeader* hdr, CloudDev* clouds, uint32_t* order, const 
         hdr->work = 0;
         hdr->n_records = 0;
         hdr->total_cells = 0;
-        for (int i = 0; i < 8; ++i) hdr->counters[i] = 0;
+        for (int i = 0; i < 9; ++i) hdr->counters[i] = 0;
         hdr->grid_arrive = 0;
         s_carry = 0;
         s_bad = 0;

@@ -37,9 +37,9 @@ struct WsHeader {
     uint32_t work;          // sampler work-queue counter
     uint32_t n_records;     // voxel records built
     uint32_t total_cells;   // sum of n_vox^3 over the clouds
-    uint64_t counters[8];   // rfps_counters fields
+    uint64_t counters[9];   // rfps_counters fields
     uint32_t grid_arrive;   // plain variant 2: grid-barrier arrival counter
-    uint32_t pad[15];
+    uint32_t pad[13];
 };
 
 constexpr int kMaxNVox = 256;

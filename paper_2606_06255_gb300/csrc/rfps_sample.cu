@@ -29,6 +29,22 @@
 // the stored distances are treated as +inf, so a reused index needs no reset.
 // There is no per-iteration kernel launch and no global-memory round trip for
 // the selection.
+//
+// Runner-up shortcut (clusters, records in shared memory).  With the exchange,
+// every CTA also learns r, the best candidate among the other warps, and each
+// warp sends, in the spare fourth coordinate, a bound on every key of its
+// records other than its own candidate (records also keep their second point
+// key for this).  Let s be the selected sample.  If d2(r) > 0, r beats the
+// winning warp's bound, and the canonical squared distance from r to s is not
+// below d2(r), then the update with s leaves r's key unchanged, lowers every
+// other key or keeps it, and sets s's own distance to 0; r is therefore
+// Alg. 1's next argmax, exactly, ties included.  Every thread evaluates the
+// same FP32 test on the same exchanged values, so the cluster agrees without
+// another exchange, and the next round applies s and r together (one visit per
+// record, the two updates in order).  On room- and LiDAR-like clouds the test
+// holds in about 97 % of the rounds, so a round selects about two samples.  The
+// second sample of a round is never the cloud's last, so a kept index still
+// ends with one pending sample.
 #include <cfloat>
 
 #include "rfps_common.cuh"
@@ -101,6 +117,7 @@ struct RecView {
     float4* ct;
     float4* best;
     unsigned long long* key;
+    unsigned long long* key2;   // second-largest point key of the record (a bound until first visited)
     uint2* rng;
     uint32_t gbase, C, nloc;
     bool perm;
@@ -117,7 +134,7 @@ struct RecView {
 };
 
 struct Cnt {
-    uint64_t tests = 0, pruned = 0, visit = 0, skip = 0, upd = 0, iter = 0;
+    uint64_t tests = 0, pruned = 0, visit = 0, skip = 0, upd = 0, iter = 0, rounds = 0;
     uint64_t pviol = 0, sviol = 0;   // shadow checks: see shadow_pruned and the skip branch below
 };
 
@@ -134,17 +151,44 @@ __device__ uint64_t shadow_pruned(const float4* pts, uint32_t off, uint32_t cnt,
     return v;
 }
 
-// One warp updates the points [off, off + cnt) of a record against s (point
-// skip, strict update, d2 write-back) and returns the lane's max key; the
-// lane's best point goes to (bx, by, bz).  `pts` / `orig` are either the CTA's
-// shared-memory copy or the workspace arrays.  PPL loads are in flight per lane.
+// The update of one point against sample s (Sec. 3.4.3 point skip, strict decrease of d2).
+template <bool COUNTERS>
+__device__ __forceinline__ void update_point(const float4& p, float sx, float sy, float sz, int skip, float& d2,
+                                             bool& write, Cnt& k)
+{
+    const float dx = __fsub_rn(p.x, sx);
+    const float dy = __fsub_rn(p.y, sy);
+    const float dz = __fsub_rn(p.z, sz);
+    const float xx = __fmul_rn(dx, dx), yy = __fmul_rn(dy, dy), zz = __fmul_rn(dz, dz);
+    if (skip && skip_point(xx, yy, zz, d2)) {
+        if (COUNTERS) {
+            ++k.skip;
+            if (__fadd_rn(__fadd_rn(xx, yy), zz) < d2) ++k.sviol;   // the skip was not exact
+        }
+    } else {
+        const float nd = __fadd_rn(__fadd_rn(xx, yy), zz);
+        if (nd < d2) {
+            d2 = nd;
+            write = true;
+            if (COUNTERS) ++k.upd;
+        }
+    }
+}
+
+// One warp updates the points [off, off + cnt) of a record against s, and then against t when
+// `two` (a round that applies two samples), with the point skip, the strict update and the d2
+// write-back.  Returns the lane's max key over its points, with that point in (bx, by, bz), and
+// the lane's second-largest key in lk2.  `pts` / `orig` are either the CTA's shared-memory copy or
+// the workspace arrays.  PPL loads are in flight per lane.
 template <int PPL, bool COUNTERS>
 __device__ __forceinline__ unsigned long long visit_points(float4* pts, const uint32_t* orig, uint32_t off,
                                                            uint32_t cnt, bool first, int skip, float sx, float sy,
                                                            float sz, int lane, float& bx, float& by, float& bz,
-                                                           Cnt& k)
+                                                           Cnt& k, bool two, float tx, float ty, float tz,
+                                                           unsigned long long& lk2)
 {
     unsigned long long lk = 0ull;
+    lk2 = 0ull;
     for (uint32_t q0 = 0; q0 < cnt; q0 += 32u * PPL) {
         float4 p[PPL];
         uint32_t gi[PPL];
@@ -161,30 +205,18 @@ __device__ __forceinline__ unsigned long long visit_points(float4* pts, const ui
             const uint32_t q = q0 + u * 32 + lane;
             if (q < cnt) {
                 float d2 = first ? __int_as_float(0x7f800000) : p[u].w;
-                const float dx = __fsub_rn(p[u].x, sx);
-                const float dy = __fsub_rn(p[u].y, sy);
-                const float dz = __fsub_rn(p[u].z, sz);
-                const float xx = __fmul_rn(dx, dx), yy = __fmul_rn(dy, dy), zz = __fmul_rn(dz, dz);
                 bool write = first;
-                if (skip && skip_point(xx, yy, zz, d2)) {
-                    if (COUNTERS) {
-                        ++k.skip;
-                        if (__fadd_rn(__fadd_rn(xx, yy), zz) < d2) ++k.sviol;   // the skip was not exact
-                    }
-                } else {
-                    const float nd = __fadd_rn(__fadd_rn(xx, yy), zz);
-                    if (nd < d2) {
-                        d2 = nd;
-                        write = true;
-                        if (COUNTERS) ++k.upd;
-                    }
-                }
+                update_point<COUNTERS>(p[u], sx, sy, sz, skip, d2, write, k);
+                if (two) update_point<COUNTERS>(p[u], tx, ty, tz, skip, d2, write, k);
                 if (write) pts[off + q].w = d2;
                 if (COUNTERS) ++k.visit;
                 const unsigned long long kk = make_key(d2, gi[u]);
                 if (kk > lk) {
+                    lk2 = lk;
                     lk = kk;
                     bx = p[u].x; by = p[u].y; bz = p[u].z;
+                } else if (kk > lk2) {
+                    lk2 = kk;
                 }
             }
         }
@@ -200,37 +232,27 @@ template <bool COUNTERS>
 __device__ __forceinline__ unsigned long long visit_points_smem(float4* pts, const uint32_t* orig, uint32_t off,
                                                                 uint32_t cnt, bool first, int skip, float sx,
                                                                 float sy, float sz, int lane, float& bx, float& by,
-                                                                float& bz, Cnt& k)
+                                                                float& bz, Cnt& k, bool two, float tx, float ty,
+                                                                float tz, unsigned long long& lk2)
 {
     unsigned long long lk = 0ull;
+    lk2 = 0ull;
 #pragma unroll 1
     for (uint32_t q = lane; q < cnt; q += 32) {
         const float4 p = pts[off + q];
         float d2 = first ? __int_as_float(0x7f800000) : p.w;
-        const float dx = __fsub_rn(p.x, sx);
-        const float dy = __fsub_rn(p.y, sy);
-        const float dz = __fsub_rn(p.z, sz);
-        const float xx = __fmul_rn(dx, dx), yy = __fmul_rn(dy, dy), zz = __fmul_rn(dz, dz);
         bool write = first;
-        if (skip && skip_point(xx, yy, zz, d2)) {
-            if (COUNTERS) {
-                ++k.skip;
-                if (__fadd_rn(__fadd_rn(xx, yy), zz) < d2) ++k.sviol;   // the skip was not exact
-            }
-        } else {
-            const float nd = __fadd_rn(__fadd_rn(xx, yy), zz);
-            if (nd < d2) {
-                d2 = nd;
-                write = true;
-                if (COUNTERS) ++k.upd;
-            }
-        }
+        update_point<COUNTERS>(p, sx, sy, sz, skip, d2, write, k);
+        if (two) update_point<COUNTERS>(p, tx, ty, tz, skip, d2, write, k);
         if (write) pts[off + q].w = d2;
         if (COUNTERS) ++k.visit;
         const unsigned long long kk = make_key(d2, orig[off + q]);
         if (kk > lk) {
+            lk2 = lk;
             lk = kk;
             bx = p.x; by = p.y; bz = p.z;
+        } else if (kk > lk2) {
+            lk2 = kk;
         }
     }
     return lk;
@@ -338,9 +360,9 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
             const uint32_t K = c.rec_end - c.rec_off;
             const uint32_t nloc = K > rank ? (K - rank + C - 1) / C : 0u;
             const uint32_t gbase = c.rec_off + rank;
-            // Fast path: every record of this CTA in shared memory (52 bytes each),
+            // Fast path: every record of this CTA in shared memory (60 bytes each),
             // then as many points as fit (20 bytes each).
-            const bool fast = static_cast<size_t>(nloc) * 52 + 16 <= a.smem_bytes && nloc <= 32u * NT;
+            const bool fast = static_cast<size_t>(nloc) * 60 + 16 <= a.smem_bytes && nloc <= 32u * NT;
             const int nb = static_cast<int>((nloc + NT - 1) / NT);   // records per lane (fast path)
             RecView<NT> v;
             v.a = &a;
@@ -372,9 +394,10 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                 v.ct = reinterpret_cast<float4*>(smem);
                 v.best = v.ct + nloc;
                 v.key = reinterpret_cast<unsigned long long*>(v.best + nloc);
-                v.rng = reinterpret_cast<uint2*>(v.key + nloc);
+                v.key2 = v.key + nloc;
+                v.rng = reinterpret_cast<uint2*>(v.key2 + nloc);
                 s_soff = reinterpret_cast<uint32_t*>(v.rng + nloc);
-                const size_t poff = (static_cast<size_t>(nloc) * 52 + 15) & ~static_cast<size_t>(15);
+                const size_t poff = (static_cast<size_t>(nloc) * 60 + 15) & ~static_cast<size_t>(15);
                 s_pts = reinterpret_cast<float4*>(smem + poff);
                 const uint32_t P = static_cast<uint32_t>((a.smem_bytes - poff) / 20);
 #ifdef RFPS_CHECKED
@@ -390,10 +413,12 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         v.ct[v.at(l)] = make_float4(sph.x, sph.y, sph.z, a.rec_thr[k]);
                         v.best[v.at(l)] = a.rec_best[k];
                         v.key[v.at(l)] = a.rec_key[k];
+                        v.key2[v.at(l)] = a.rec_key[k];   // a bound until the record's next visit
                     } else {
                         v.ct[v.at(l)] = make_float4(sph.x, sph.y, sph.z, nan);
                         v.best[v.at(l)] = make_float4(0.f, 0.f, 0.f, sph.w);
                         v.key[v.at(l)] = 0ull;
+                        v.key2[v.at(l)] = 0ull;   // every record is visited in the first iteration
                     }
                     v.rng[v.at(l)] = rg;
                     mine += rg.y;
@@ -523,8 +548,12 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                 s_rlcut[1] = W;
             }
             if (rank == 0 && t == 0 && !resume) a.out[c.out_off] = c.start;
-            // this lane's cached max over the records it owns (my, my + NT, ...)
-            unsigned long long lkey = 0ull;
+            // a second sample applied in the same round (the runner-up shortcut, below)
+            bool two = false;
+            float tx = 0.f, ty = 0.f, tz = 0.f;
+            // this lane's cached max over the records it owns (my, my + NT, ...), and a bound on
+            // every other key of them (the second-largest of their key and key2 values)
+            unsigned long long lkey = 0ull, lkey2 = 0ull;
             uint32_t lrec = 0xffffffffu;
             bool dirty = true;
             __syncthreads();
@@ -546,34 +575,40 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                 // counting runs: the shadow check of a pruned record held by this CTA
                 auto shadow_record = [&](uint32_t l) -> uint64_t {
                     const uint2 rg = v.rng[Q(l)];
-                    return (resident && (rg.x & kResident)) ? shadow_pruned(s_pts, rg.x & ~kResident, rg.y, sx, sy, sz)
-                                                            : shadow_pruned(a.pts4, rg.x, rg.y, sx, sy, sz);
+                    float4* base = (resident && (rg.x & kResident)) ? s_pts : a.pts4;
+                    const uint32_t off = (resident && (rg.x & kResident)) ? (rg.x & ~kResident) : rg.x;
+                    return shadow_pruned(base, off, rg.y, sx, sy, sz) + (two ? shadow_pruned(base, off, rg.y, tx, ty, tz) : 0);
                 };
                 if constexpr (NREG > 0) {
                     if (my < nloc) ct0 = v.ct[Q(my)];
                     if (NREG == 2 && my + NT < nloc) ct1 = v.ct[Q(my + NT)];
                 }
-                for (int64_t j = 1; j < c.m; ++j) {
+                int64_t rnd = 0;   // rounds so far (a round selects one or two samples)
+                for (int64_t j = 1; j < c.m; ++rnd) {
                     const bool first = (j == 1) && !resume;   // the initial update of Sec. 3.3
-                    const int par = static_cast<int>(j & 1);
+                    const int par = static_cast<int>(rnd & 1);
                     unsigned long long pk;   // this lane's partial max (key, record) for the selection
+                    unsigned long long pk2;  // a bound on this lane's other keys
                     uint32_t prec;
                     uint32_t vis = 0;        // my records visited now (bit b: record b * NT + my)
                     // a visited record's bookkeeping waits until the warp's candidate is pushed
                     uint32_t dl = 0xffffffffu;
-                    unsigned long long dk = 0ull;
+                    unsigned long long dk = 0ull, dk2 = 0ull;
                     float dx = 0.f, dy = 0.f, dz = 0.f;
                     bool ppt = false;        // this lane's candidate is a point of a record visited now
                     float px = 0.f, py = 0.f, pz = 0.f;
-                    auto finish_record = [&](uint32_t l, unsigned long long lk, float bx, float by, float bz) {
+                    auto finish_record = [&](uint32_t l, unsigned long long lk, unsigned long long lk2, float bx,
+                                             float by, float bz) {
                         unsigned long long rk;
                         const int rl = warp_argmax_lane(lk, &rk);
+                        const unsigned long long rk2 = warp_max_u64(lane == rl ? lk2 : lk);   // second point key
                         const float wx = __shfl_sync(0xffffffffu, bx, rl);
                         const float wy = __shfl_sync(0xffffffffu, by, rl);
                         const float wz = __shfl_sync(0xffffffffu, bz, rl);
                         if (lane == 0) {
                             const float r = v.best[Q(l)].w;
                             v.key[Q(l)] = rk;
+                            v.key2[Q(l)] = rk2;
                             v.best[Q(l)] = make_float4(wx, wy, wz, r);
                             v.ct[Q(l)].w = prune_threshold(r, rk);
                         }
@@ -583,8 +618,10 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         uint32_t um = 0;
                         if constexpr (NREG > 0) {
                             const bool h0 = my < nloc, h1 = NREG == 2 && my + NT < nloc;
-                            const bool k0 = h0 && (first || !a.prune || !prune_by_threshold(ct0, sx, sy, sz));
-                            const bool k1 = h1 && (first || !a.prune || !prune_by_threshold(ct1, sx, sy, sz));
+                            const bool k0 = h0 && (first || !a.prune || !prune_by_threshold(ct0, sx, sy, sz) ||
+                                                   (two && !prune_by_threshold(ct0, tx, ty, tz)));
+                            const bool k1 = h1 && (first || !a.prune || !prune_by_threshold(ct1, sx, sy, sz) ||
+                                                   (two && !prune_by_threshold(ct1, tx, ty, tz)));
                             um = (k0 ? 1u : 0u) | (k1 ? 2u : 0u);
                             if (COUNTERS && !first) {
                                 cn.tests += (h0 ? 1 : 0) + (h1 ? 1 : 0);
@@ -596,7 +633,9 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             for (int b = 0; b < nb; ++b) {
                                 const uint32_t l = static_cast<uint32_t>(b) * NT + my;
                                 if (l < nloc) {
-                                    const bool keep = first || !a.prune || !prune_by_threshold(v.ct[Q(l)], sx, sy, sz);
+                                    const float4 ctl = v.ct[Q(l)];
+                                    const bool keep = first || !a.prune || !prune_by_threshold(ctl, sx, sy, sz) ||
+                                                      (two && !prune_by_threshold(ctl, tx, ty, tz));
                                     um |= keep ? (1u << b) : 0u;
                                     if (COUNTERS && !first) {
                                         ++cn.tests;
@@ -610,14 +649,18 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         const bool lrec_visited = lrec != 0xffffffffu && ((um >> (lrec / NT)) & 1u);
                         if (dirty || lrec_visited) {
                             lkey = 0ull;
+                            lkey2 = 0ull;
                             lrec = 0xffffffffu;
                             for (int b = 0; b < (NREG > 0 ? NREG : nb); ++b) {
                                 const uint32_t l = static_cast<uint32_t>(b) * NT + my;
                                 if (l < nloc && !((um >> b) & 1u)) {
                                     const unsigned long long kk = v.key[Q(l)];
                                     if (kk > lkey) {
+                                        lkey2 = max(lkey, v.key2[Q(l)]);
                                         lkey = kk;
                                         lrec = l;
+                                    } else {
+                                        lkey2 = max(lkey2, kk);
                                     }
                                 }
                             }
@@ -625,6 +668,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         dirty = um != 0;
                         vis = um;
                         pk = lkey;
+                        pk2 = lkey2;
                         prec = lrec;
                         // ---- one warp per unpruned record: every warp visits the records its own lanes
                         // hold (record l belongs to slot l mod NT, and consecutive records, which are
@@ -642,6 +686,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             if (!RFPS_IN(l < nloc)) continue;
                             const uint2 rg = v.rng[Q(l)];
                             float bx = 0.f, by = 0.f, bz = 0.f;
+                            unsigned long long lk2 = 0ull;
                             const bool in_smem = resident && (rg.x & kResident);
 #ifdef RFPS_CHECKED
                             if (!RFPS_IN(in_smem ? (rg.x & ~kResident) + rg.y <= pcap
@@ -650,25 +695,31 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
 #endif
                             const unsigned long long lk =
                                 !in_smem ? visit_points<PPL, COUNTERS>(a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx,
-                                                                       sy, sz, lane, bx, by, bz, cn)
+                                                                       sy, sz, lane, bx, by, bz, cn, two, tx, ty, tz, lk2)
                                 : NT >= 512 ? visit_points_smem<COUNTERS>(s_pts, s_orig, rg.x & ~kResident, rg.y,
-                                                                          first, a.skip, sx, sy, sz, lane, bx, by, bz, cn)
+                                                                          first, a.skip, sx, sy, sz, lane, bx, by, bz, cn,
+                                                                          two, tx, ty, tz, lk2)
                                             : visit_points<PPL, COUNTERS>(s_pts, s_orig, rg.x & ~kResident, rg.y, first,
-                                                                          a.skip, sx, sy, sz, lane, bx, by, bz, cn);
+                                                                          a.skip, sx, sy, sz, lane, bx, by, bz, cn, two,
+                                                                          tx, ty, tz, lk2);
                             if constexpr (CLUSTER) {
                                 // the candidate may now be a visited point (its coordinates are in
                                 // registers); the record's own update waits until the candidate is
                                 // pushed, overlapping the exchange (one record pending at most)
                                 if (lk > pk) {
+                                    pk2 = max(pk, lk2);
                                     pk = lk;
                                     ppt = true;
                                     px = bx;
                                     py = by;
                                     pz = bz;
+                                } else {
+                                    pk2 = max(pk2, lk);
                                 }
-                                if (dl != 0xffffffffu) finish_record(dl, dk, dx, dy, dz);
+                                if (dl != 0xffffffffu) finish_record(dl, dk, dk2, dx, dy, dz);
                                 dl = l;
                                 dk = lk;
+                                dk2 = lk2;
                                 dx = bx;
                                 dy = by;
                                 dz = bz;
@@ -706,8 +757,10 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             if (!RFPS_IN(static_cast<uint64_t>(rg.x) + rg.y <= a.n_total)) return;
 #endif
                             float bx = 0.f, by = 0.f, bz = 0.f;
+                            unsigned long long lk2;
                             const unsigned long long lk = visit_points<PPL, COUNTERS>(
-                                a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx, sy, sz, lane, bx, by, bz, cn);
+                                a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx, sy, sz, lane, bx, by, bz, cn, false, 0.f,
+                                0.f, 0.f, lk2);
                             const int wl = warp_argmax_lane(lk, &rk);
                             wx = __shfl_sync(0xffffffffu, bx, wl);
                             wy = __shfl_sync(0xffffffffu, by, wl);
@@ -910,6 +963,10 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     }
                     unsigned long long wk;
                     const int wl = warp_argmax_lane(pk, &wk);
+                    // every key of this warp's records other than its candidate is at most wb (the
+                    // runner-up shortcut below needs it; the hierarchical path gives no bound)
+                    float wbd = __int_as_float(0x7f800000);
+                    if constexpr (FAST && CLUSTER) wbd = key_d2(warp_max_u64(lane == wl ? pk2 : pk));
                     const uint32_t wr = OWN_XYZ ? 0u : __shfl_sync(0xffffffffu, prec, wl);
                     bool wpt = false;                 // the warp's candidate coordinates are in vxyz
                     float4 vxyz = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -928,6 +985,9 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     }
                     float4 cxyz = make_float4(0.f, 0.f, 0.f, 0.f);
                     unsigned long long gbest;
+                    bool nsc = false;                 // the next round applies two samples
+                    unsigned long long nk2 = 0ull;
+                    float ntx = 0.f, nty = 0.f, ntz = 0.f;
                     if (!CLUSTER) {
                         // each warp publishes its candidate's key and coordinates (the record's owner
                         // may rewrite its best point in the next iteration, before a slower warp reads it)
@@ -957,6 +1017,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         if (wpt) wxyz = vxyz;
                         else if (wk != 0ull && lane < static_cast<int>(C) && RFPS_IN(wr < (FAST ? nloc : G)))
                             wxyz = FAST ? v.best[Q(wr)] : s_sxyz[wr];
+                        wxyz.w = wbd;
                         // (counting kernels: a lost round sends nothing, so its waits run out)
                         if (lane < static_cast<int>(C) && !(COUNTERS && j == a.lost_iter)) {
                             const uint32_t rb = buf ? rbar1 : rbar0;
@@ -964,7 +1025,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             st_async_f32x4(buf ? rxyz1 : rxyz0, wxyz, rb);
                         }
                         if constexpr (FAST) {   // the last visited record's update overlaps the exchange
-                            if (dl != 0xffffffffu) finish_record(dl, dk, dx, dy, dz);
+                            if (dl != 0xffffffffu) finish_record(dl, dk, dk2, dx, dy, dz);
                             __syncwarp();
                             if constexpr (NREG > 0) {   // thresholds rewritten by this iteration's visits
                                 if (vis & 1u) ct0.w = v.ct[Q(my)].w;
@@ -983,8 +1044,8 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         // arrive by shuffle instead of a shared load after the reduction (measured
                         // faster there, slower with 256 threads, whose lanes read four slots each)
                         constexpr bool SLOT_XYZ = NT == 128;
-                        unsigned long long kk = 0ull;
-                        uint32_t ki = 0;
+                        unsigned long long kk = 0ull, kk2 = 0ull;
+                        uint32_t ki = 0, ki2 = 0;
                         float4 kx = make_float4(0.f, 0.f, 0.f, 0.f);
     #pragma unroll
                         for (int u = 0; u < NSLOT / 32; ++u) {   // every slot, unrolled; unused ones read as 0
@@ -995,12 +1056,36 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                                 if (q < nslot) xq = s_cxyz[buf][q];
                             }
                             if (x > kk) {
+                                kk2 = kk;
+                                ki2 = ki;
                                 kk = x;
                                 ki = q;
                                 kx = xq;
+                            } else if (x > kk2) {
+                                kk2 = x;
+                                ki2 = q;
                             }
                         }
                         const int gl = warp_argmax_lane(kk, &gbest);
+                        if constexpr (FAST) {
+                            // Runner-up shortcut (exact): r, the best of the other slots, is the next
+                            // sample if every other key is below it (the winning warp's bound), its
+                            // distance is positive, and the update by this sample leaves it unchanged:
+                            // every other key only decreases, and this sample's own becomes 0.
+                            unsigned long long rk2;
+                            const int gl2 = warp_argmax_lane(lane == gl ? kk2 : kk, &rk2);
+                            const uint32_t si = __shfl_sync(0xffffffffu, lane == gl ? ki2 : ki, gl2);
+                            const uint32_t wi = __shfl_sync(0xffffffffu, ki, gl);
+                            const float4 r4 = s_cxyz[buf][si];
+                            const float4 w4 = s_cxyz[buf][wi];
+                            const float rd = key_d2(rk2);
+                            nsc = j + 2 < c.m && !(COUNTERS && a.lost_iter != 0) && rk2 != 0ull && rd > 0.f &&
+                                  rd > w4.w && sq_dist(r4.x, r4.y, r4.z, w4.x, w4.y, w4.z) >= rd;
+                            nk2 = rk2;
+                            ntx = r4.x;
+                            nty = r4.y;
+                            ntz = r4.z;
+                        }
                         if constexpr (SLOT_XYZ) {
                             cxyz.x = __shfl_sync(0xffffffffu, kx.x, gl);
                             cxyz.y = __shfl_sync(0xffffffffu, kx.y, gl);
@@ -1013,9 +1098,20 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     sx = cxyz.x;
                     sy = cxyz.y;
                     sz = cxyz.z;
-                    if (rank == 0 && t == 0)
+                    if (rank == 0 && t == 0) {
                         a.out[c.out_off + (resume ? j - 1 : j)] = static_cast<int64_t>(key_index(gbest)) - c.pt_off;
-                    if (COUNTERS) ++cn.iter;
+                        if (nsc) a.out[c.out_off + (resume ? j : j + 1)] = static_cast<int64_t>(key_index(nk2)) - c.pt_off;
+                    }
+                    two = nsc;
+                    tx = ntx;
+                    ty = nty;
+                    tz = ntz;
+                    const int64_t step = nsc ? 2 : 1;
+                    if (COUNTERS) {
+                        cn.iter += static_cast<uint64_t>(step);
+                        ++cn.rounds;
+                    }
+                    j += step;
                 }
             };
             if (!fast) iterate(IntC<0>{});
@@ -1069,7 +1165,10 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[2]), cn.visit);
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[3]), cn.skip);
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[4]), cn.upd);
-        if (t == 0 && rank == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[5]), cn.iter);
+        if (t == 0 && rank == 0) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[5]), cn.iter);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[8]), cn.rounds);
+        }
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[6]), cn.pviol);
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[7]), cn.sviol);
     }
@@ -1357,7 +1456,10 @@ __global__ void __launch_bounds__(NT, 1) k_sample_regs(const SampleArgs a)
                 sz = cxyz.z;
                 if (t == 0)
                     a.out[c.out_off + (resume ? j - 1 : j)] = static_cast<int64_t>(key_index(gbest)) - c.pt_off;
-                if (COUNTERS && t == 0) ++cn.iter;
+                if (COUNTERS && t == 0) {
+                    ++cn.iter;
+                    ++cn.rounds;
+                }
             }
             if (a.save_state) {   // the distances and the last sample, for a later resume
 #pragma unroll
@@ -1378,7 +1480,10 @@ __global__ void __launch_bounds__(NT, 1) k_sample_regs(const SampleArgs a)
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[2]), cn.visit);
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[3]), cn.skip);
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[4]), cn.upd);
-        if (t == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[5]), cn.iter);
+        if (t == 0) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[5]), cn.iter);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[8]), cn.rounds);
+        }
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[6]), cn.pviol);
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.hdr->counters[7]), cn.sviol);
     }

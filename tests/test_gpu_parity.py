@@ -247,6 +247,29 @@ def test_counters(rf):
     assert c["points_visited"] < 0.2 * 50000 * 4999
 
 
+
+@pytest.mark.parametrize("opts,shortcut", [({"cluster": 16, "threads": 128, "chunk": 64}, True),
+                                            ({"cluster": 4, "threads": 256}, True),
+                                            ({"cluster": 1, "threads": 256}, False)],
+                         ids=["c16_t128", "c4_t256", "one_cta"])
+def test_runner_up_shortcut_rounds(rf, opts, shortcut):
+    """Clusters select the exchange's runner-up as the next sample when the new sample leaves it
+    unchanged: fewer exchange rounds than samples, the oracle's indices all the same.  A single CTA
+    selects one sample a round."""
+    pts = cloudgen.room_cloud(40000, seed=33)
+    m = 6000
+    o = dict(opts, counters=1)
+    ws = torch.empty(rf.workspace_size(40000, o), dtype=torch.uint8, device="cuda")
+    out = rf.fps(dev(pts), m, 5, opts=o, workspace=ws)
+    c = rf.counters(ws)
+    np.testing.assert_array_equal(out.cpu().numpy(), oracle.fps(pts, m, 5, threads=0))
+    assert c["iterations"] == m - 1
+    if shortcut:
+        assert (m - 1) / 2 <= c["rounds"] < 0.75 * (m - 1), c
+    else:
+        assert c["rounds"] == m - 1
+    assert c["prune_violations"] == 0 and c["skip_violations"] == 0
+
 SHADOW_CASES = [
     ("room_20k_c16_t128", lambda: cloudgen.room_cloud(20000, seed=81), 3000, {"cluster": 16, "threads": 128}),
     ("room_20k_c1", lambda: cloudgen.room_cloud(20000, seed=82), 3000, {"cluster": 1}),

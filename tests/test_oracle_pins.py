@@ -109,3 +109,47 @@ def test_radiusfps_prunes_and_skips():
     assert st["voxels_pruned"] > 0.9 * st["voxel_tests"]
     assert st["points_skipped"] > 0
     assert st["points_updated"] < st["points_visited"]
+
+
+def _canonical_d2(p, q):
+    d = (p - q).astype(np.float32)
+    return ((d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]).astype(np.float32)
+
+
+@pytest.mark.parametrize("kind", ["room", "lidar", "lattice", "duplicates"])
+def test_runner_up_shortcut_matches_the_oracle(kind):
+    """The sampling kernel's runner-up shortcut, checked against the oracle's FPS sequence: whenever
+    the runner-up r of the state that chose s_j (second-largest (d2, lowest index) key) has d2 > 0
+    and its canonical squared distance to s_j is not below its d2, the oracle's next sample is r.
+    Ties (the lattice) and zero distances (duplicates) are the cases the d2 > 0 and key rules
+    exist for."""
+    rng = np.random.default_rng(5)
+    n, m = 3000, 700
+    if kind == "room":
+        pts = cloudgen.room_cloud(n, seed=61)
+    elif kind == "lidar":
+        pts = cloudgen.lidar_cloud(n, seed=62)
+    elif kind == "lattice":
+        g = np.arange(15, dtype=np.float32)
+        pts = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)[:n].astype(np.float32)
+    else:
+        base = rng.random((n // 4, 3), dtype=np.float32)
+        pts = np.repeat(base, 4, axis=0)
+        m = n // 4 + 50   # past the distinct points: the remaining distances are 0
+    pts = np.ascontiguousarray(pts, dtype=np.float32)
+    seq = oracle.fps(pts, m, 0)
+    d2 = np.full(pts.shape[0], np.inf, dtype=np.float32)
+    idx = np.arange(pts.shape[0])
+    fired = 0
+    for j in range(1, m - 1):
+        nd = _canonical_d2(pts, pts[seq[j - 1]])
+        d2 = np.where(nd < d2, nd, d2)
+        # (d2, lowest index) order: the oracle's next sample is the first key, r the second
+        order = np.lexsort((idx, -d2.astype(np.float64)))
+        t1, r = order[0], order[1]
+        assert t1 == seq[j]
+        if d2[r] > 0 and _canonical_d2(pts[r], pts[t1]) >= d2[r]:
+            fired += 1
+            assert seq[j + 1] == r, (j, r, seq[j + 1])
+    # with four copies of every point the runner-up is a copy of the sample (distance 0): never taken
+    assert fired > 0 if kind != "duplicates" else fired == 0
