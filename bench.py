@@ -199,9 +199,10 @@ def ncu_traffic(workload, opts):
         return None
     with open(p) as fh:
         d = json.load(fh)
-    if d.get("kernel_hash") != kernel_hash() or (d.get("opts") or None) != (opts or None):
-        return None
-    return d.get("dram_bytes_per_launch")
+    for cap in d.get("captures", [d]):   # one capture, or several launch shapes of the workload
+        if cap.get("kernel_hash") == kernel_hash() and (cap.get("opts") or None) == (opts or None):
+            return cap.get("dram_bytes_per_launch")
+    return None
 
 
 def workload_config(name, seed=0):
