@@ -86,9 +86,12 @@ typedef struct {
 typedef struct {
     uint64_t voxel_tests;     /* voxel-record prune tests */
     uint64_t voxels_pruned;   /* records skipped by Eq. radius_pruning_condition */
-    uint64_t points_visited;  /* points of unpruned records */
-    uint64_t points_skipped;  /* points dropped by Eq. point_skip_condition */
-    uint64_t points_updated;  /* strict decreases of a stored distance (effective updates) */
+    uint64_t points_visited;  /* points of unpruned records, once per visit (a visit applies
+                                 the one or two samples of its round) */
+    uint64_t points_skipped;  /* visited points dropped by Eq. point_skip_condition for every
+                                 sample the visit applied */
+    uint64_t points_updated;  /* visited points whose stored distance decreased (effective
+                                 updates) */
     uint64_t iterations;      /* sampling iterations (selections after the start point) */
     uint64_t prune_violations; /* shadow check: points of pruned records whose distance to the
                                   new sample was below their stored one (0 when the bound is safe) */

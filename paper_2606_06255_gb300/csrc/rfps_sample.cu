@@ -44,7 +44,9 @@
 // record, the two updates in order).  On room- and LiDAR-like clouds the test
 // holds in about 97 % of the rounds, so a round selects about two samples.  The
 // second sample of a round is never the cloud's last, so a kept index still
-// ends with one pending sample.
+// ends with one pending sample.  The register-record kernel for small clouds
+// applies the same rule over the warps of its one CTA (a thread's record is its
+// points, its second key the second largest of their keys).
 #include <cfloat>
 
 #include "rfps_common.cuh"
@@ -152,27 +154,34 @@ __device__ uint64_t shadow_pruned(const float4* pts, uint32_t off, uint32_t cnt,
 }
 
 // The update of one point against sample s (Sec. 3.4.3 point skip, strict decrease of d2).
+// `skipped` is cleared when the skip does not apply; `write` is set when d2 decreased.
 template <bool COUNTERS>
 __device__ __forceinline__ void update_point(const float4& p, float sx, float sy, float sz, int skip, float& d2,
-                                             bool& write, Cnt& k)
+                                             bool& write, bool& skipped, Cnt& k)
 {
     const float dx = __fsub_rn(p.x, sx);
     const float dy = __fsub_rn(p.y, sy);
     const float dz = __fsub_rn(p.z, sz);
     const float xx = __fmul_rn(dx, dx), yy = __fmul_rn(dy, dy), zz = __fmul_rn(dz, dz);
     if (skip && skip_point(xx, yy, zz, d2)) {
-        if (COUNTERS) {
-            ++k.skip;
-            if (__fadd_rn(__fadd_rn(xx, yy), zz) < d2) ++k.sviol;   // the skip was not exact
-        }
+        if (COUNTERS && __fadd_rn(__fadd_rn(xx, yy), zz) < d2) ++k.sviol;   // the skip was not exact
     } else {
+        skipped = false;
         const float nd = __fadd_rn(__fadd_rn(xx, yy), zz);
         if (nd < d2) {
             d2 = nd;
             write = true;
-            if (COUNTERS) ++k.upd;
         }
     }
+}
+
+// Work counters of one visited point: skipped when every sample of the round skipped it, updated
+// when its distance decreased (the visit counts the point once, however many samples it applies).
+__device__ __forceinline__ void count_point(Cnt& k, bool skipped, bool updated)
+{
+    ++k.visit;
+    if (skipped) ++k.skip;
+    if (updated) ++k.upd;
 }
 
 // One warp updates the points [off, off + cnt) of a record against s, and then against t when
@@ -205,11 +214,12 @@ __device__ __forceinline__ unsigned long long visit_points(float4* pts, const ui
             const uint32_t q = q0 + u * 32 + lane;
             if (q < cnt) {
                 float d2 = first ? __int_as_float(0x7f800000) : p[u].w;
-                bool write = first;
-                update_point<COUNTERS>(p[u], sx, sy, sz, skip, d2, write, k);
-                if (two) update_point<COUNTERS>(p[u], tx, ty, tz, skip, d2, write, k);
+                const float d0 = d2;
+                bool write = first, skipped = true;
+                update_point<COUNTERS>(p[u], sx, sy, sz, skip, d2, write, skipped, k);
+                if (two) update_point<COUNTERS>(p[u], tx, ty, tz, skip, d2, write, skipped, k);
                 if (write) pts[off + q].w = d2;
-                if (COUNTERS) ++k.visit;
+                if (COUNTERS) count_point(k, skipped, d2 < d0);
                 const unsigned long long kk = make_key(d2, gi[u]);
                 if (kk > lk) {
                     lk2 = lk;
@@ -241,11 +251,12 @@ __device__ __forceinline__ unsigned long long visit_points_smem(float4* pts, con
     for (uint32_t q = lane; q < cnt; q += 32) {
         const float4 p = pts[off + q];
         float d2 = first ? __int_as_float(0x7f800000) : p.w;
-        bool write = first;
-        update_point<COUNTERS>(p, sx, sy, sz, skip, d2, write, k);
-        if (two) update_point<COUNTERS>(p, tx, ty, tz, skip, d2, write, k);
+        const float d0 = d2;
+        bool write = first, skipped = true;
+        update_point<COUNTERS>(p, sx, sy, sz, skip, d2, write, skipped, k);
+        if (two) update_point<COUNTERS>(p, tx, ty, tz, skip, d2, write, skipped, k);
         if (write) pts[off + q].w = d2;
-        if (COUNTERS) ++k.visit;
+        if (COUNTERS) count_point(k, skipped, d2 < d0);
         const unsigned long long kk = make_key(d2, orig[off + q]);
         if (kk > lk) {
             lk2 = lk;
@@ -1347,18 +1358,21 @@ __global__ void __launch_bounds__(NT, 1) k_sample_regs(const SampleArgs a)
                 if (q0 + u < n) m = fmaxf(m, __fsqrt_rn(sq_dist(px[u], py[u], pz[u], cx, cy, cz)));
             const float rad = fmaxf(__fmul_rn(m, 0x1.00001p0f), 0x1p-50f);
             // Dist_v key of the record and its point, from the distances it starts with (+inf, or the
-            // saved ones); it changes only when a distance does
-            unsigned long long key = 0ull;
+            // saved ones), and the second-largest point key; they change only when a distance does
+            unsigned long long key = 0ull, key2 = 0ull;
             float bx = 0.f, by = 0.f, bz = 0.f;
 #pragma unroll
             for (int u = 0; u < P; ++u) {
                 if (q0 + u < n) {
                     const unsigned long long kk = make_key(pd[u], po[u]);
                     if (kk > key) {
+                        key2 = key;
                         key = kk;
                         bx = px[u];
                         by = py[u];
                         bz = pz[u];
+                    } else if (kk > key2) {
+                        key2 = kk;
                     }
                 }
             }
@@ -1368,98 +1382,135 @@ __global__ void __launch_bounds__(NT, 1) k_sample_regs(const SampleArgs a)
             float sy = resume ? c.last[1] : a.pts[3 * g0 + 1];
             float sz = resume ? c.last[2] : a.pts[3 * g0 + 2];
             if (t == 0 && !resume) a.out[c.out_off] = c.start;
-            for (int64_t j = 1; grouped && j < c.m; ++j) {   // (a cloud that failed its checks: none)
+            // a second sample applied in the same round (the runner-up shortcut of k_sample's
+            // clusters, here over the CTA's warps)
+            bool two = false;
+            float tx = 0.f, ty = 0.f, tz = 0.f;
+            int64_t rnd = 0;
+            for (int64_t j = 1; grouped && j < c.m; ++rnd) {   // (a cloud that failed its checks: none)
                 const bool first = (j == 1) && !resume;
-                const int par = static_cast<int>(j & 1);
-                const bool keep = has && (first || !a.prune || !prune_by_threshold(ct, sx, sy, sz));
+                const int par = static_cast<int>(rnd & 1);
+                const bool keep_s = has && (first || !a.prune || !prune_by_threshold(ct, sx, sy, sz));
+                const bool keep_t = has && two && (!a.prune || !prune_by_threshold(ct, tx, ty, tz));
                 if (COUNTERS && !first && has) {
                     ++cn.tests;
-                    if (!keep) {
-                        ++cn.pruned;
+                    if (!keep_s && !keep_t) ++cn.pruned;
 #pragma unroll
-                        for (int u = 0; u < P; ++u)   // shadow check: no pruned point may improve
-                            if (q0 + u < n && sq_dist(px[u], py[u], pz[u], sx, sy, sz) < pd[u]) ++cn.pviol;
+                    for (int u = 0; u < P; ++u) {   // shadow check: no pruned point may improve
+                        if (q0 + u < n && !keep_s && sq_dist(px[u], py[u], pz[u], sx, sy, sz) < pd[u]) ++cn.pviol;
+                        if (q0 + u < n && two && !keep_t && sq_dist(px[u], py[u], pz[u], tx, ty, tz) < pd[u]) ++cn.pviol;
                     }
                 }
-                if (keep) {
+                if (keep_s || keep_t) {
                     bool changed = false;
 #pragma unroll
                     for (int u = 0; u < P; ++u) {
                         if (q0 + u < n) {
-                            const float dx = __fsub_rn(px[u], sx);
-                            const float dy = __fsub_rn(py[u], sy);
-                            const float dz = __fsub_rn(pz[u], sz);
-                            const float xx = __fmul_rn(dx, dx), yy = __fmul_rn(dy, dy), zz = __fmul_rn(dz, dz);
-                            if (a.skip && skip_point(xx, yy, zz, pd[u])) {
-                                if (COUNTERS) {
-                                    ++cn.skip;
-                                    if (__fadd_rn(__fadd_rn(xx, yy), zz) < pd[u]) ++cn.sviol;
-                                }
-                            } else {
-                                const float nd = __fadd_rn(__fadd_rn(xx, yy), zz);
-                                if (nd < pd[u]) {
-                                    pd[u] = nd;
-                                    changed = true;
-                                    if (COUNTERS) ++cn.upd;
+                            const float d0 = pd[u];
+                            bool sk = true;   // every applied sample skipped the point
+#pragma unroll
+                            for (int q = 0; q < 2; ++q) {   // the round's samples in order
+                                if (q == 0 ? !keep_s : !keep_t) continue;
+                                const float dx = __fsub_rn(px[u], q == 0 ? sx : tx);
+                                const float dy = __fsub_rn(py[u], q == 0 ? sy : ty);
+                                const float dz = __fsub_rn(pz[u], q == 0 ? sz : tz);
+                                const float xx = __fmul_rn(dx, dx), yy = __fmul_rn(dy, dy), zz = __fmul_rn(dz, dz);
+                                if (a.skip && skip_point(xx, yy, zz, pd[u])) {
+                                    if (COUNTERS && __fadd_rn(__fadd_rn(xx, yy), zz) < pd[u]) ++cn.sviol;
+                                } else {
+                                    sk = false;
+                                    const float nd = __fadd_rn(__fadd_rn(xx, yy), zz);
+                                    if (nd < pd[u]) {
+                                        pd[u] = nd;
+                                        changed = true;
+                                    }
                                 }
                             }
-                            if (COUNTERS) ++cn.visit;
+                            if (COUNTERS) {
+                                ++cn.visit;
+                                if (sk) ++cn.skip;
+                                if (pd[u] < d0) ++cn.upd;
+                            }
                         }
                     }
                     // the Dist_v key and threshold change only when a distance did
                     if (changed) {
-                        // max over the points' keys as a pairwise tree (empty slots give key 0)
-                        unsigned long long tk[P];
-                        float tx[P], ty[P], tz[P];
+                        // max and second max over the points' keys as a pairwise tree (empty slots
+                        // give key 0)
+                        unsigned long long tk[P], t2[P];
+                        float ux[P], uy[P], uz[P];
 #pragma unroll
                         for (int u = 0; u < P; ++u) {
                             tk[u] = q0 + u < n ? make_key(pd[u], po[u]) : 0ull;
-                            tx[u] = px[u];
-                            ty[u] = py[u];
-                            tz[u] = pz[u];
+                            t2[u] = 0ull;
+                            ux[u] = px[u];
+                            uy[u] = py[u];
+                            uz[u] = pz[u];
                         }
 #pragma unroll
                         for (int h = 1; h < P; h <<= 1) {
 #pragma unroll
                             for (int u = 0; u + h < P; u += 2 * h) {
                                 if (tk[u + h] > tk[u]) {
+                                    t2[u] = max(tk[u], t2[u + h]);
                                     tk[u] = tk[u + h];
-                                    tx[u] = tx[u + h];
-                                    ty[u] = ty[u + h];
-                                    tz[u] = tz[u + h];
+                                    ux[u] = ux[u + h];
+                                    uy[u] = uy[u + h];
+                                    uz[u] = uz[u + h];
+                                } else {
+                                    t2[u] = max(t2[u], tk[u + h]);
                                 }
                             }
                         }
                         key = tk[0];
-                        bx = tx[0];
-                        by = ty[0];
-                        bz = tz[0];
+                        key2 = t2[0];
+                        bx = ux[0];
+                        by = uy[0];
+                        bz = uz[0];
                         ct.w = prune_threshold(rad, key);
                     }
                 }
-                // selection: warp argmax, one CTA barrier, argmax over the warps
+                // selection: warp argmax, one CTA barrier, argmax over the warps.  Each warp also
+                // publishes a bound on its other keys (the winning lane's second key, the other
+                // lanes' keys) for the runner-up shortcut.
                 unsigned long long wk;
                 const int wl = warp_argmax_lane(key, &wk);
+                const float wbd = key_d2(warp_max_u64(lane == wl ? key2 : key));
                 const float wx = __shfl_sync(0xffffffffu, bx, wl);
                 const float wy = __shfl_sync(0xffffffffu, by, wl);
                 const float wz = __shfl_sync(0xffffffffu, bz, wl);
                 if (lane == 0) {
                     s_wkey[par][w] = wk;
-                    s_wxyz[par][w] = make_float4(wx, wy, wz, 0.f);
+                    s_wxyz[par][w] = make_float4(wx, wy, wz, wbd);
                 }
                 __syncthreads();
-                unsigned long long gbest;
-                const int cl = warp_argmax_lane(lane < NW ? s_wkey[par][lane] : 0ull, &gbest);
+                unsigned long long gbest, rk2;
+                const unsigned long long ck = lane < NW ? s_wkey[par][lane] : 0ull;
+                const int cl = warp_argmax_lane(ck, &gbest);
+                const int cl2 = warp_argmax_lane(lane == cl ? 0ull : ck, &rk2);   // the best of the other warps
                 const float4 cxyz = s_wxyz[par][cl];
+                const float4 rxyz = s_wxyz[par][cl2];
                 sx = cxyz.x;
                 sy = cxyz.y;
                 sz = cxyz.z;
-                if (t == 0)
+                // the runner-up r is the next sample too (exact) if it beats the winning warp's bound,
+                // its distance is positive and the update with this sample leaves it unchanged
+                const float rd = key_d2(rk2);
+                const bool nsc = j + 2 < c.m && rk2 != 0ull && rd > 0.f && rd > cxyz.w &&
+                                 sq_dist(rxyz.x, rxyz.y, rxyz.z, cxyz.x, cxyz.y, cxyz.z) >= rd;
+                if (t == 0) {
                     a.out[c.out_off + (resume ? j - 1 : j)] = static_cast<int64_t>(key_index(gbest)) - c.pt_off;
+                    if (nsc) a.out[c.out_off + (resume ? j : j + 1)] = static_cast<int64_t>(key_index(rk2)) - c.pt_off;
+                }
+                two = nsc;
+                tx = rxyz.x;
+                ty = rxyz.y;
+                tz = rxyz.z;
                 if (COUNTERS && t == 0) {
-                    ++cn.iter;
+                    cn.iter += nsc ? 2 : 1;
                     ++cn.rounds;
                 }
+                j += nsc ? 2 : 1;
             }
             if (a.save_state) {   // the distances and the last sample, for a later resume
 #pragma unroll

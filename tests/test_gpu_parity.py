@@ -248,18 +248,20 @@ def test_counters(rf):
 
 
 
-@pytest.mark.parametrize("opts,shortcut", [({"cluster": 16, "threads": 128, "chunk": 64}, True),
-                                            ({"cluster": 4, "threads": 256}, True),
-                                            ({"cluster": 1, "threads": 256}, False)],
-                         ids=["c16_t128", "c4_t256", "one_cta"])
-def test_runner_up_shortcut_rounds(rf, opts, shortcut):
-    """Clusters select the exchange's runner-up as the next sample when the new sample leaves it
-    unchanged: fewer exchange rounds than samples, the oracle's indices all the same.  A single CTA
-    selects one sample a round."""
-    pts = cloudgen.room_cloud(40000, seed=33)
-    m = 6000
+@pytest.mark.parametrize("opts,n,shortcut", [({"cluster": 16, "threads": 128, "chunk": 64}, 40000, True),
+                                              ({"cluster": 4, "threads": 256}, 40000, True),
+                                              ({"cluster": 1, "threads": 256}, 40000, False),
+                                              ({"cluster": 1, "threads": 512}, 4000, True)],
+                         ids=["c16_t128", "c4_t256", "one_cta", "register_records"])
+def test_runner_up_shortcut_rounds(rf, opts, n, shortcut):
+    """Clusters, and the register-record kernel for small clouds, select the runner-up as the next
+    sample too when the new sample leaves it unchanged: fewer selection rounds than samples, the
+    oracle's indices all the same.  The shared-memory loop of a single CTA selects one sample a
+    round."""
+    pts = cloudgen.room_cloud(n, seed=33)
+    m = n * 3 // 20
     o = dict(opts, counters=1)
-    ws = torch.empty(rf.workspace_size(40000, o), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(rf.workspace_size(n, o), dtype=torch.uint8, device="cuda")
     out = rf.fps(dev(pts), m, 5, opts=o, workspace=ws)
     c = rf.counters(ws)
     np.testing.assert_array_equal(out.cpu().numpy(), oracle.fps(pts, m, 5, threads=0))
