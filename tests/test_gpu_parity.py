@@ -529,3 +529,22 @@ def test_distance_state_every_iteration_small(rf, name, make, opts):
         d = ix.distances().cpu().numpy()
         np.testing.assert_array_equal(d.view(np.uint32), np.asarray(rd, np.float32).view(np.uint32), err_msg=f"m={m}")
     ix.free()
+
+
+@pytest.mark.parametrize("opts", [{"cluster": 4, "threads": 256}, {"cluster": 16, "threads": 128},
+                                  {"cluster": 1, "threads": 512}], ids=["c4", "c16", "register_records"])
+def test_runner_up_shortcut_at_the_sequence_ends(rf, opts):
+    """The runner-up shortcut never takes a cloud's last sample, so short runs and every resume
+    boundary of a kept index still give the oracle's sequence: M = 1 to 6, and pieces of one to
+    five samples continued with sample_more."""
+    n = 4000 if opts["cluster"] == 1 else 30000
+    pts = cloudgen.room_cloud(n, seed=57)
+    ref = oracle.fps(pts, 60, 11, threads=0)
+    for m in range(1, 7):
+        np.testing.assert_array_equal(gpu_fps(rf, pts, m, 11, **opts), ref[:m])
+    ix = rf.Index(dev(pts), opts=opts)
+    got = [ix.sample(3, 11).cpu().numpy()]
+    for k in (1, 2, 3, 4, 5, 1, 2, 3, 4, 5, 1, 2, 3, 4, 5, 1):
+        got.append(ix.sample_more(k).cpu().numpy())
+    np.testing.assert_array_equal(np.concatenate(got), ref[:sum(len(g) for g in got)])
+    ix.free()
