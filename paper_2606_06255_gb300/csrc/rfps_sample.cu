@@ -30,8 +30,9 @@
 // There is no per-iteration kernel launch and no global-memory round trip for
 // the selection.
 //
-// Runner-up shortcut (clusters, records in shared memory).  With the exchange,
-// every CTA also learns r, the best candidate among the other warps, and each
+// Runner-up shortcut (records in shared memory, on a cluster or one CTA).  With
+// the exchange (or, on one CTA, the warps' shared slots), every CTA also learns
+// r, the best candidate among the other warps, and each
 // warp sends, in the spare fourth coordinate, a bound on every key of its
 // records other than its own candidate (records also keep their second point
 // key for this).  Let s be the selected sample.  If d2(r) > 0, r beats the
@@ -739,17 +740,22 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                                 // the update, so it is done here and merged into lane 0's candidate
                                 unsigned long long rk;
                                 const int rl = warp_argmax_lane(lk, &rk);
+                                const unsigned long long rk2 = warp_max_u64(lane == rl ? lk2 : lk);
                                 const float wx = __shfl_sync(0xffffffffu, bx, rl);
                                 const float wy = __shfl_sync(0xffffffffu, by, rl);
                                 const float wz = __shfl_sync(0xffffffffu, bz, rl);
                                 if (lane == 0) {
                                     const float r = v.best[Q(l)].w;
                                     v.key[Q(l)] = rk;
+                                    v.key2[Q(l)] = rk2;
                                     v.best[Q(l)] = make_float4(wx, wy, wz, r);
                                     v.ct[Q(l)].w = prune_threshold(r, rk);
                                     if (rk > pk) {
+                                        pk2 = max(pk, rk2);
                                         pk = rk;
                                         prec = l;
+                                    } else {
+                                        pk2 = max(pk2, rk);
                                     }
                                 }
                             }
@@ -977,7 +983,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     // every key of this warp's records other than its candidate is at most wb (the
                     // runner-up shortcut below needs it; the hierarchical path gives no bound)
                     float wbd = __int_as_float(0x7f800000);
-                    if constexpr (FAST && CLUSTER) wbd = key_d2(warp_max_u64(lane == wl ? pk2 : pk));
+                    if constexpr (FAST) wbd = key_d2(warp_max_u64(lane == wl ? pk2 : pk));
                     const uint32_t wr = OWN_XYZ ? 0u : __shfl_sync(0xffffffffu, prec, wl);
                     bool wpt = false;                 // the warp's candidate coordinates are in vxyz
                     float4 vxyz = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1004,8 +1010,10 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         // may rewrite its best point in the next iteration, before a slower warp reads it)
                         if (lane == 0) {
                             s_wkey[par][w] = wk;
-                            s_wxyz[par][w] = wk != 0ull && RFPS_IN(wr < (FAST ? nloc : G))
-                                                 ? (FAST ? v.best[Q(wr)] : s_sxyz[wr]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            float4 b4 = wk != 0ull && RFPS_IN(wr < (FAST ? nloc : G))
+                                            ? (FAST ? v.best[Q(wr)] : s_sxyz[wr]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            b4.w = wbd;   // this warp's bound on its other keys
+                            s_wxyz[par][w] = b4;
                         }
                         if constexpr (NREG > 0) {   // thresholds rewritten by this iteration's visits
                             if (vis & 1u) ct0.w = v.ct[Q(my)].w;
@@ -1015,6 +1023,18 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         const unsigned long long ck = lane < NW ? s_wkey[par][lane] : 0ull;
                         const int cl = warp_argmax_lane(ck, &gbest);
                         cxyz = s_wxyz[par][cl];
+                        if constexpr (FAST) {   // the runner-up shortcut over the CTA's warps
+                            unsigned long long rk2;
+                            const int cl2 = warp_argmax_lane(lane == cl ? 0ull : ck, &rk2);
+                            const float4 r4 = s_wxyz[par][cl2];
+                            const float rd = key_d2(rk2);
+                            nsc = j + 2 < c.m && rk2 != 0ull && rd > 0.f && rd > cxyz.w &&
+                                  sq_dist(r4.x, r4.y, r4.z, cxyz.x, cxyz.y, cxyz.z) >= rd;
+                            nk2 = rk2;
+                            ntx = r4.x;
+                            nty = r4.y;
+                            ntz = r4.z;
+                        }
                     } else {
                         // Every warp pushes its best (key, xyz) by st.async into slot [rank][warp] of every
                         // CTA; each CTA's barrier for this round expects C * NW * 24 bytes.  (Reducing in the
