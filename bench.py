@@ -402,17 +402,21 @@ def measure_batch64(args, rf, torch, world=1, rank=0):
     sizes = [c.points.shape[0] for c in clouds]
     ms = [c.m for c in clouds]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    tuned = None
+    tuned = split_tuned = None
+    split = None
     if args.opts:
-        opts = json.loads(args.opts)
+        opts = single_opts = json.loads(args.opts)
     else:
         # launch shape and automatic-resolution scale picked by the autotuner on this batch (the
         # voxel resolution follows each cloud's size); every candidate gives the same indices
         cat0 = torch.from_numpy(np.ascontiguousarray(np.concatenate([c.points for c in clouds]), np.float32)).cuda()
-        opts, table = rf.autotune.tune_batch(cat0, sizes, ms, reps=2)
+        single_opts, table = rf.autotune.tune_batch(cat0, sizes, ms, reps=2)
         tuned = [{"ms": round(t, 3), "opts": o} for t, o in table[:8]]
         del cat0
-    bs = rf.batch.BatchSampler(sizes, ms, opts=opts)
+        # then the single launch against size splits (the largest clouds in a concurrent launch)
+        (opts, split), stable = rf.autotune.tune_batch_split([c.points for c in clouds], sizes, ms, single_opts)
+        split_tuned = [{"ms": round(t, 3), "opts": o, "split": sp} for t, o, sp in stable[:6]]
+    bs = rf.batch.BatchSampler(sizes, ms, opts=opts, split=split)
     bs.load([c.points for c in clouds])
     for _ in range(max(args.warmup, 3)):
         bs.run()
@@ -431,16 +435,20 @@ def measure_batch64(args, rf, torch, world=1, rank=0):
         return {"metric": "clouds/s", "value": len(all_clouds) / (t_batch / 1e3), "unit": "clouds/s",
                 "config": config, "n_gpus": world, "scaling": "strong", "clouds_rank0": len(clouds),
                 "ms_per_batch": t_batch, "samples_per_s": sum(c.m for c in all_clouds) / (t_batch / 1e3),
-                "opts_rank0": opts, "graph": True, "gpu_launches_per_batch_rank0": launches}
-    ref = bs.out.cpu().numpy()
-    cat, off = bs.points, bs.offsets
+                "opts_rank0": opts, "split_rank0": split, "graph": True,
+                "gpu_launches_per_batch_rank0": launches}
+    ref = np.concatenate(bs.split())   # the caller's cloud order
+    cat = torch.from_numpy(np.ascontiguousarray(np.concatenate([c.points for c in clouds]), np.float32)).cuda()
+    meta = rf._lib._batch_meta(sizes, ms, None, cat.device)
+    off = meta[3]
     views = [cat[int(off[b]):int(off[b + 1])] for b in range(len(sizes))]
-    wss = [torch.empty(rf.workspace_size(sizes[b], opts), dtype=torch.uint8, device="cuda") for b in range(len(sizes))]
+    wss = [torch.empty(rf.workspace_size(sizes[b], single_opts), dtype=torch.uint8, device="cuda")
+           for b in range(len(sizes))]
     outs = [torch.empty(ms[b], dtype=torch.int64, device="cuda") for b in range(len(sizes))]
 
     def per_cloud():
         for b in range(len(sizes)):
-            rf.fps(views[b], ms[b], 0, opts=opts, workspace=wss[b], out=outs[b])
+            rf.fps(views[b], ms[b], 0, opts=single_opts, workspace=wss[b], out=outs[b])
     per_cloud()
     t_sep = _events(torch, per_cloud, 2, flush)
     same = bool(np.array_equal(np.concatenate([o.cpu().numpy() for o in outs]), ref))
@@ -449,11 +457,11 @@ def measure_batch64(args, rf, torch, world=1, rank=0):
     for v in (1, 0):
         res = {}
         t = _events(torch, lambda: res.setdefault("o", rf.plain_fps_batched(cat, sizes, ms, variant=v, workspace=pws,
-                                                                           meta=bs.meta)[0]), 1, flush)
+                                                                           meta=meta)[0]), 1, flush)
         plain[f"variant{v}"] = {"ms": t, "clouds_per_s": len(sizes) / (t / 1e3)}
     return {"metric": "clouds/s", "value": len(sizes) / (t_batch / 1e3), "unit": "clouds/s", "config": config,
-            "ms_per_batch": t_batch, "samples_per_s": sum(ms) / (t_batch / 1e3), "opts": opts, "autotune": tuned,
-            "graph": True, "gpu_launches_per_batch": launches,
+            "ms_per_batch": t_batch, "samples_per_s": sum(ms) / (t_batch / 1e3), "opts": opts, "split": split,
+            "autotune": tuned, "split_autotune": split_tuned, "graph": True, "gpu_launches_per_batch": launches,
             "per_cloud_launches": {"ms": t_sep, "clouds_per_s": len(sizes) / (t_sep / 1e3), "same_indices": same},
             "batched_vs_per_cloud": t_sep / t_batch, "plain_batched": plain,
             "batched_vs_plain_batched": min(p["ms"] for p in plain.values()) / t_batch}

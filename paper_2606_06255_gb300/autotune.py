@@ -123,6 +123,54 @@ def tune_batch(points: torch.Tensor, sizes, ms, starts=None, candidates=None, re
     return _two_stage(time_one, candidates or default_candidates(True), scales)
 
 
+def split_candidates(sizes, base_opts):
+    """Size splits of a ragged batch to time against its single launch: the k largest clouds (k = 5,
+    8, 10) in a launch of their own on 16- or 8-CTA clusters, the rest on 4-CTA clusters or with the
+    single launch's options."""
+    order = sorted(sizes, reverse=True)
+    cands = []
+    for k in (5, 8, 10):
+        if k >= len(order):
+            continue
+        tail_n = order[k - 1]
+        if order[k] >= tail_n:   # no clean cut between the k-th and (k+1)-th largest
+            continue
+        for tail_opts in ({"cluster": 16, "threads": 256, "chunk": 128}, {"cluster": 8, "threads": 256, "chunk": 128}):
+            for rest in ({"cluster": 4, "threads": 256, "chunk": 128}, dict(base_opts or {})):
+                cands.append((dict(rest), {"tail_n": int(tail_n), "tail_opts": tail_opts}))
+    return cands
+
+
+def tune_batch_split(clouds, sizes, ms, base_opts, reps: int = 3, candidates=None):
+    """Time the single graph-replayed launch of a ragged batch against size splits (BatchSampler's
+    split: the largest clouds in a concurrent launch of their own); returns ((opts, split or None),
+    [(ms, opts, split), ...]) sorted by time.  Every candidate gives the same indices."""
+    from . import batch
+
+    def time_one(opts, split):
+        bs = batch.BatchSampler(sizes, ms, opts=opts, split=split)
+        bs.load(clouds)
+        for _ in range(2):
+            bs.run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            bs.run()
+        e1.record()
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / reps
+        return t if bs.status() == 0 else math.inf
+
+    table = [(time_one(dict(base_opts or {}), None), dict(base_opts or {}), None)]
+    for opts, split in (candidates if candidates is not None else split_candidates(sizes, base_opts)):
+        table.append((time_one(opts, split), opts, split))
+    table.sort(key=lambda r: r[0])
+    if not math.isfinite(table[0][0]):
+        raise RuntimeError("no batch launch candidate ran without a device error")
+    return (table[0][1], table[0][2]), table
+
+
 def load_cache(path: str = DEFAULT_CACHE) -> dict:
     if not os.path.exists(path):
         return {}

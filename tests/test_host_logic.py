@@ -402,3 +402,24 @@ def test_cpu_baseline_reports_the_three_oracle_timings():
     assert c["kind"] == "oracle" and c["value"] > 0 and c["cores"] >= 1
     assert c["plain_1thread"]["cores"] == 1 and c["plain_1thread"]["value"] > 0
     assert c["radiusfps_1thread"]["n_vox"] == 32 and c["radiusfps_1thread"]["value"] > 0
+
+
+def test_batch_split_layout():
+    """A size-split batch keeps each group's clouds contiguous (the tail group first) and maps every
+    cloud back to its rows and output range in the caller's order."""
+    from paper_2606_06255_gb300 import batch
+    sizes = [5000, 120000, 800, 90000, 200000, 3000]
+    ms = [s // 4 for s in sizes]
+    bs = batch.BatchSampler(sizes, ms, opts={"cluster": 4}, device="cpu", graph=False,
+                            split={"tail_n": 90000, "tail_opts": {"cluster": 16, "threads": 256}})
+    assert [g.ids for g in bs.groups] == [[1, 3, 4], [0, 2, 5]]
+    assert bs.groups[0].opts == {"cluster": 16, "threads": 256} and bs.groups[1].opts == {"cluster": 4}
+    rows = sorted(bs.rows)
+    assert rows[0][0] == 0 and rows[-1][1] == sum(sizes)
+    assert all(a[1] == b[0] for a, b in zip(rows, rows[1:]))           # a partition of the buffer
+    assert all(hi - lo == n for (lo, hi), n in zip(bs.rows, sizes))
+    assert all(hi - lo == m for (lo, hi), m in zip(bs.out_rows, ms))
+    assert max(bs.rows[i][1] for i in (1, 3, 4)) <= min(bs.rows[i][0] for i in (0, 2, 5))   # tail group first
+    # no split: one group in the caller's order
+    one = batch.BatchSampler(sizes, ms, device="cpu", graph=False)
+    assert len(one.groups) == 1 and one.rows[0] == (0, 5000) and one.rows[1] == (5000, 125000)
