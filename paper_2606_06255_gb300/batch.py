@@ -14,6 +14,8 @@ that runs beside the first group's on a second stream; both launches, the fork
 and the join are captured in the same graph.  Each group's clouds sit
 contiguously in the point buffer (tail group first), so `rows` gives each
 cloud's rows there; `split()` returns the indices in the caller's cloud order.
+Without a split the sampler also exposes its single launch's `meta`, `offsets`,
+`out_offsets` and `workspace`; with one, each of `groups` holds its own.
 """
 
 from __future__ import annotations
