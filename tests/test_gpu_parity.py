@@ -464,6 +464,39 @@ def test_fuzz_single_cloud(rf, seed):
                                   err_msg=f"{kind} n={n} m={m} start={start} {o}")
 
 
+def _tie_cloud(rng, kind, n):
+    """Clouds full of exactly equal squared distances: small-integer coordinates, mirror images, a
+    ring of equally spaced points around equal blobs, a coarse quantised grid."""
+    if kind == "integers":
+        return rng.integers(0, 6, size=(n, 3)).astype(np.float32)
+    if kind == "mirrored":
+        half = cloudgen.uniform_cloud(max(1, n // 2), seed=int(rng.integers(1 << 30)))
+        return np.concatenate([half, -half])[:n]
+    if kind == "ring":
+        k = max(3, n // 40)
+        ang = 2 * np.pi * np.arange(k) / k
+        centres = np.stack([np.cos(ang), np.sin(ang), np.zeros(k)], 1) * 64
+        blob = rng.integers(-2, 3, size=(max(1, n // k), 3))
+        return (centres[:, None, :] + blob[None, :, :]).reshape(-1, 3)[:n].astype(np.float32)
+    return np.round(cloudgen.room_cloud(n, seed=int(rng.integers(1 << 30))) * 4) / 4   # quantised
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_fuzz_ties(rf, seed):
+    """Exact ties everywhere (the case the runner-up shortcut's strict bound and d2 > 0 rule guard):
+    seeded tie-heavy clouds under random options, the register-record path included."""
+    rng = np.random.default_rng(3000 + seed)
+    kind = ["integers", "mirrored", "ring", "quantised"][seed % 4]
+    n = int(np.exp(rng.uniform(np.log(50), np.log(30000))))
+    pts = np.ascontiguousarray(_tie_cloud(rng, kind, n), dtype=np.float32)
+    n = pts.shape[0]
+    m = int(rng.integers(1, min(n, 2500) + 1))
+    start = int(rng.integers(0, n))
+    o = {"cluster": 1, "threads": 512} if seed % 3 == 0 else _fuzz_opts(rng)
+    np.testing.assert_array_equal(gpu_fps(rf, pts, m, start, **o), oracle.fps(pts, m, start, threads=0),
+                                  err_msg=f"{kind} n={n} m={m} start={start} {o}")
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_fuzz_batched(rf, seed):
     """Seeded random ragged batches (kinds, sizes, M, starts) under a random option set."""
