@@ -47,7 +47,10 @@
 // second sample of a round is never the cloud's last, so a kept index still
 // ends with one pending sample.  The register-record kernel for small clouds
 // applies the same rule over the warps of its one CTA (a thread's record is its
-// points, its second key the second largest of their keys).
+// points, its second key the second largest of their keys), and the
+// hierarchical path over super-records: a record in global memory keeps its
+// second-key bound in rec_best.w (its radius is rec_sph.w), and a super-record
+// keeps a bound on its keys but the max, refreshed with it.
 #include <cfloat>
 
 #include "rfps_common.cuh"
@@ -394,6 +397,8 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
             float4* s_sxyz = nullptr;            // best point of the super, radius in .w
             unsigned long long* s_skey = nullptr;
             uint32_t* s_slist = nullptr;         // unpruned super-records of this iteration
+            float* s_sk2 = nullptr;              // per super-record: bound on its keys but the max (d2)
+            float* s_rk2 = nullptr;              // per record-list entry: the visit's second-key bound
             uint2* s_sent = nullptr;             // per super-record: its range in the record list
             // record list (unpruned records of this iteration): local record, point range, and
             // the new key and best point its visit produced
@@ -423,7 +428,8 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     const uint2 rg = a.rec_rng[k];
                     if (resume) {   // saved state: threshold, best point (radius in .w), key
                         v.ct[v.at(l)] = make_float4(sph.x, sph.y, sph.z, a.rec_thr[k]);
-                        v.best[v.at(l)] = a.rec_best[k];
+                        const float4 rb = a.rec_best[k];
+                        v.best[v.at(l)] = make_float4(rb.x, rb.y, rb.z, sph.w);
                         v.key[v.at(l)] = a.rec_key[k];
                         v.key2[v.at(l)] = a.rec_key[k];   // a bound until the record's next visit
                     } else {
@@ -473,31 +479,40 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                 // records' spheres, the max of their Dist_v keys and the coordinates of the point
                 // that attains it, kept in shared memory.  Pruning tests super-records first.
                 G = (nloc + 31) / 32;
-                if (static_cast<size_t>(G) * 52 + 16 > a.smem_bytes) {
+                if (static_cast<size_t>(G) * 56 + 16 > a.smem_bytes) {
                     // more records than one CTA can index (beyond ~140k per CTA): larger clusters
                     // or records are needed; record the error and skip the cloud uniformly
                     if (t == 0) atomicCAS(&a.hdr->status, 0u, kStatusUnsupported);
                     G = 0;
                 }
-                // 52 bytes per super-record (16-byte arrays first), then 36 per record-list entry
+                // 56 bytes per super-record (16-byte arrays first), then 40 per record-list entry
                 s_sct = reinterpret_cast<float4*>(smem);
                 s_sxyz = s_sct + G;
                 s_skey = reinterpret_cast<unsigned long long*>(s_sxyz + G);
                 s_sent = reinterpret_cast<uint2*>(s_skey + G);
                 s_slist = reinterpret_cast<uint32_t*>(s_sent + G);
-                const size_t used = (static_cast<size_t>(G) * 52 + 15) & ~static_cast<size_t>(15);
-                const size_t room = a.smem_bytes > used ? (a.smem_bytes - used) / 36 : 0;
+                s_sk2 = reinterpret_cast<float*>(s_slist + G);
+                const size_t used = (static_cast<size_t>(G) * 56 + 15) & ~static_cast<size_t>(15);
+                const size_t room = a.smem_bytes > used ? (a.smem_bytes - used) / 40 : 0;
                 W = static_cast<uint32_t>(room < nloc ? room : nloc);
                 s_rxyz = reinterpret_cast<float4*>(smem + used);
                 s_rkey = reinterpret_cast<unsigned long long*>(s_rxyz + W);
                 s_rrng = reinterpret_cast<uint2*>(s_rkey + W);
                 s_rlist = reinterpret_cast<uint32_t*>(s_rrng + W);
-                if (!resume) {
-                    for (uint32_t l = t; l < nloc; l += NT) {
-                        const uint32_t k = v.g(l);
+                s_rk2 = reinterpret_cast<float*>(s_rlist + W);
+                // records in global memory keep, in rec_best.w, a bound on the squared distances of their
+                // points but the best one (the runner-up shortcut's second key); on a resume it is reset
+                // to the record's max, a safe bound until the record's next visit
+                for (uint32_t l = t; l < nloc; l += NT) {
+                    const uint32_t k = v.g(l);
+                    if (!resume) {
                         a.rec_thr[k] = nan;
                         a.rec_key[k] = 0ull;
-                        a.rec_best[k] = make_float4(0.f, 0.f, 0.f, a.rec_sph[k].w);
+                        a.rec_best[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    } else {
+                        float4 rb = a.rec_best[k];
+                        rb.w = key_d2(a.rec_key[k]);
+                        a.rec_best[k] = rb;
                     }
                 }
                 __syncthreads();
@@ -543,6 +558,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         s_sct[g] = make_float4(cs[0], cs[1], cs[2], resume ? prune_threshold(srad, gk) : nan);
                         s_sxyz[g] = make_float4(bxyz.x, bxyz.y, bxyz.z, srad);
                         s_skey[g] = gk;
+                        s_sk2[g] = key_d2(gk);   // safe until the super-record is refreshed
                     }
                 }
             }
@@ -764,9 +780,10 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         // one warp updates record l (global memory; point range rg, covering radius r):
                         // its points' distances, then its key, best point and prune threshold in global
                         // memory.  The new key and best point are returned to every lane.
-                        auto visit_global = [&](uint32_t l, uint2 rg, float r, unsigned long long& rk, float& wx,
-                                                float& wy, float& wz) {
+                        auto visit_global = [&](uint32_t l, uint2 rg, float r, unsigned long long& rk, float& rk2d,
+                                                float& wx, float& wy, float& wz) {
                             rk = 0ull;
+                            rk2d = 0.f;
                             wx = wy = wz = 0.f;
                             if (!RFPS_IN(l < nloc)) return;
                             const uint32_t k = v.g(l);
@@ -776,15 +793,16 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             float bx = 0.f, by = 0.f, bz = 0.f;
                             unsigned long long lk2;
                             const unsigned long long lk = visit_points<PPL, COUNTERS>(
-                                a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx, sy, sz, lane, bx, by, bz, cn, false, 0.f,
-                                0.f, 0.f, lk2);
+                                a.pts4, a.porig, rg.x, rg.y, first, a.skip, sx, sy, sz, lane, bx, by, bz, cn, two, tx,
+                                ty, tz, lk2);
                             const int wl = warp_argmax_lane(lk, &rk);
+                            rk2d = key_d2(warp_max_u64(lane == wl ? lk2 : lk));
                             wx = __shfl_sync(0xffffffffu, bx, wl);
                             wy = __shfl_sync(0xffffffffu, by, wl);
                             wz = __shfl_sync(0xffffffffu, bz, wl);
                             if (lane == 0) {
                                 a.rec_key[k] = rk;
-                                a.rec_best[k] = make_float4(wx, wy, wz, r);
+                                a.rec_best[k] = make_float4(wx, wy, wz, rk2d);
                                 a.rec_thr[k] = prune_threshold(r, rk);
                             }
                         };
@@ -794,7 +812,8 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             for (int b = 0; b < 32; ++b) {
                                 const uint32_t g = g0s + static_cast<uint32_t>(b) * NT + my;
                                 if (g >= G) break;
-                                const bool keep = first || !a.prune || !prune_by_threshold(s_sct[g], sx, sy, sz);
+                                const bool keep = first || !a.prune || !prune_by_threshold(s_sct[g], sx, sy, sz) ||
+                                                  (two && !prune_by_threshold(s_sct[g], tx, ty, tz));
                                 su |= keep ? (1u << b) : 0u;
                                 if (COUNTERS && !first) {
                                     ++cn.tests;
@@ -802,7 +821,8 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                                     if (!keep) {   // every record of the pruned super-record
                                         for (uint32_t l = g * 32; l < min(nloc, g * 32 + 32); ++l) {
                                             const uint2 rg = a.rec_rng[v.g(l)];
-                                            cn.pviol += shadow_pruned(a.pts4, rg.x, rg.y, sx, sy, sz);
+                                            cn.pviol += shadow_pruned(a.pts4, rg.x, rg.y, sx, sy, sz) +
+                                                        (two ? shadow_pruned(a.pts4, rg.x, rg.y, tx, ty, tz) : 0);
                                         }
                                     }
                                 }
@@ -846,6 +866,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             uint2 rg = make_uint2(0u, 0u);
                             unsigned long long kk = 0ull;
                             float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                            float rad = 0.f;
                             if (l < nloc) {
                                 const uint32_t k = v.g(l);
                                 const float4 sp = a.rec_sph[k];
@@ -853,15 +874,24 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                                 rg = a.rec_rng[k];
                                 kk = a.rec_key[k];
                                 b4 = a.rec_best[k];
-                                keep = first || !a.prune || !prune_by_threshold(make_float4(sp.x, sp.y, sp.z, thr), sx, sy, sz);
+                                rad = sp.w;
+                                const float4 ctr = make_float4(sp.x, sp.y, sp.z, thr);
+                                keep = first || !a.prune || !prune_by_threshold(ctr, sx, sy, sz) ||
+                                       (two && !prune_by_threshold(ctr, tx, ty, tz));
                                 if (COUNTERS && !first) {
                                     ++cn.tests;
                                     cn.pruned += keep ? 0 : 1;
-                                    if (!keep && a.prune) cn.pviol += shadow_pruned(a.pts4, rg.x, rg.y, sx, sy, sz);
+                                    if (!keep && a.prune)
+                                        cn.pviol += shadow_pruned(a.pts4, rg.x, rg.y, sx, sy, sz) +
+                                                    (two ? shadow_pruned(a.pts4, rg.x, rg.y, tx, ty, tz) : 0);
                                 }
                             }
                             unsigned long long pmk;
                             const int pl = warp_argmax_lane(keep ? 0ull : kk, &pmk);
+                            // bound on the unchanged records' keys but pmk: the others' maxima and pmk's
+                            // record's second key
+                            float sk2d = fmaxf(key_d2(warp_max_u64(keep || lane == pl ? 0ull : kk)),
+                                               pmk != 0ull ? __shfl_sync(0xffffffffu, b4.w, pl) : 0.f);
                             float px4 = __shfl_sync(0xffffffffu, b4.x, pl);
                             float py4 = __shfl_sync(0xffffffffu, b4.y, pl);
                             float pz4 = __shfl_sync(0xffffffffu, b4.z, pl);
@@ -876,7 +906,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                                         const uint32_t e = base + __popc(mask & ((1u << lane) - 1u));
                                         s_rlist[e] = l;
                                         s_rrng[e] = rg;
-                                        s_rxyz[e] = make_float4(0.f, 0.f, 0.f, b4.w);
+                                        s_rxyz[e] = make_float4(0.f, 0.f, 0.f, rad);
                                     }
                                     ent = make_uint2(base, static_cast<uint32_t>(__popc(mask)));
                                 } else {
@@ -887,21 +917,25 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                                         mask &= mask - 1;
                                         const uint2 rs = make_uint2(__shfl_sync(0xffffffffu, rg.x, src),
                                                                     __shfl_sync(0xffffffffu, rg.y, src));
-                                        const float rr = __shfl_sync(0xffffffffu, b4.w, src);
+                                        const float rr = __shfl_sync(0xffffffffu, rad, src);
                                         unsigned long long rk;
-                                        float wx, wy, wz;
-                                        visit_global(g * 32 + static_cast<uint32_t>(src), rs, rr, rk, wx, wy, wz);
+                                        float rk2d, wx, wy, wz;
+                                        visit_global(g * 32 + static_cast<uint32_t>(src), rs, rr, rk, rk2d, wx, wy, wz);
                                         if (rk > pmk) {
+                                            sk2d = fmaxf(sk2d, fmaxf(key_d2(pmk), rk2d));
                                             pmk = rk;
                                             px4 = wx;
                                             py4 = wy;
                                             pz4 = wz;
+                                        } else {
+                                            sk2d = fmaxf(sk2d, key_d2(rk));
                                         }
                                     }
                                 }
                             }
                             if (lane == 0) {
                                 s_skey[g] = pmk;
+                                s_sk2[g] = sk2d;
                                 s_sxyz[g] = make_float4(px4, py4, pz4, s_sxyz[g].w);
                                 s_sent[g] = ent;
                             }
@@ -912,10 +946,11 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         for (uint32_t e = w; e < nrl; e += NW) {
                             const float r = s_rxyz[e].w;
                             unsigned long long rk;
-                            float wx, wy, wz;
-                            visit_global(s_rlist[e], s_rrng[e], r, rk, wx, wy, wz);
+                            float rk2d, wx, wy, wz;
+                            visit_global(s_rlist[e], s_rrng[e], r, rk, rk2d, wx, wy, wz);
                             if (lane == 0) {
                                 s_rkey[e] = rk;
+                                s_rk2[e] = rk2d;
                                 s_rxyz[e] = make_float4(wx, wy, wz, r);
                             }
                         }
@@ -928,35 +963,52 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             const uint2 ent = s_sent[g];
                             if (!RFPS_IN(ent.x + ent.y <= W)) continue;
                             unsigned long long kk = 0ull;
-                            float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                            float k2d = 0.f;
                             if (static_cast<uint32_t>(lane) < ent.y) {
                                 kk = s_rkey[ent.x + lane];
-                                b4 = s_rxyz[ent.x + lane];
+                                k2d = s_rk2[ent.x + lane];
                             }
                             unsigned long long gk;
                             const int gl = warp_argmax_lane(kk, &gk);
+                            // the visited records' other keys: the second-largest max and the winner's
+                            // second key
+                            const float vk2d = fmaxf(key_d2(warp_max_u64(lane == gl ? 0ull : kk)),
+                                                     __shfl_sync(0xffffffffu, k2d, gl));
                             if (lane == 0) {
                                 const unsigned long long pmk = s_skey[g];   // unchanged records (A2)
                                 float4 bx = s_sxyz[g];
                                 const float srad = bx.w;
-                                if (gk > pmk) bx = s_rxyz[ent.x + gl];
-                                else gk = pmk;
+                                float sk2d = s_sk2[g];                        // their other keys (A2)
+                                if (gk > pmk) {
+                                    bx = s_rxyz[ent.x + gl];
+                                    sk2d = fmaxf(fmaxf(sk2d, key_d2(pmk)), vk2d);
+                                } else {
+                                    sk2d = fmaxf(sk2d, key_d2(gk));
+                                    gk = pmk;
+                                }
                                 s_skey[g] = gk;
+                                s_sk2[g] = sk2d;
                                 s_sxyz[g] = make_float4(bx.x, bx.y, bx.z, srad);
                                 s_sct[g].w = prune_threshold(srad, gk);
                             }
                         }
                         __syncthreads();
-                        // ---- D: my super-records' max
+                        // ---- D: my super-records' max, and a bound on every other key of them (the
+                        // second-largest max, and the winner's bound, as the largest key of that distance)
                         pk = 0ull;
+                        pk2 = 0ull;
                         prec = 0xffffffffu;
                         for (uint32_t g = my; g < G; g += NT) {
                             const unsigned long long kk = s_skey[g];
                             if (kk > pk) {
+                                pk2 = pk;
                                 pk = kk;
                                 prec = g;
+                            } else if (kk > pk2) {
+                                pk2 = kk;
                             }
                         }
+                        if (prec != 0xffffffffu) pk2 = max(pk2, make_key(s_sk2[prec], 0u));
                     }
                     // ---- selection: warp -> CTA -> cluster
                     __syncwarp();
@@ -983,7 +1035,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                     // every key of this warp's records other than its candidate is at most wb (the
                     // runner-up shortcut below needs it; the hierarchical path gives no bound)
                     float wbd = __int_as_float(0x7f800000);
-                    if constexpr (FAST) wbd = key_d2(warp_max_u64(lane == wl ? pk2 : pk));
+                    wbd = key_d2(warp_max_u64(lane == wl ? pk2 : pk));
                     const uint32_t wr = OWN_XYZ ? 0u : __shfl_sync(0xffffffffu, prec, wl);
                     bool wpt = false;                 // the warp's candidate coordinates are in vxyz
                     float4 vxyz = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1023,7 +1075,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                         const unsigned long long ck = lane < NW ? s_wkey[par][lane] : 0ull;
                         const int cl = warp_argmax_lane(ck, &gbest);
                         cxyz = s_wxyz[par][cl];
-                        if constexpr (FAST) {   // the runner-up shortcut over the CTA's warps
+                        {   // the runner-up shortcut over the CTA's warps
                             unsigned long long rk2;
                             const int cl2 = warp_argmax_lane(lane == cl ? 0ull : ck, &rk2);
                             const float4 r4 = s_wxyz[par][cl2];
@@ -1098,7 +1150,7 @@ __global__ void __launch_bounds__(NT, 1) k_sample(const SampleArgs a)
                             }
                         }
                         const int gl = warp_argmax_lane(kk, &gbest);
-                        if constexpr (FAST) {
+                        {
                             // Runner-up shortcut (exact): r, the best of the other slots, is the next
                             // sample if every other key is below it (the winning warp's bound), its
                             // distance is positive, and the update by this sample leaves it unchanged:

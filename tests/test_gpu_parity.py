@@ -252,13 +252,16 @@ def test_counters(rf):
                                               ({"cluster": 4, "threads": 256}, 40000, True),
                                               ({"cluster": 1, "threads": 256}, 40000, True),
                                               ({"cluster": 1, "threads": 512}, 4000, True),
-                                              ({"cluster": 1, "threads": 256, "chunk": 32, "n_vox": 40}, 60000, False)],
-                         ids=["c16_t128", "c4_t256", "one_cta", "register_records", "hierarchical"])
+                                              ({"cluster": 1, "threads": 256, "chunk": 32, "n_vox": 40}, 60000, True),
+                                              ({"cluster": 1, "threads": 256, "chunk": 32, "n_vox": 40, "prune": 0},
+                                               60000, True)],
+                         ids=["c16_t128", "c4_t256", "one_cta", "register_records", "hierarchical",
+                              "hierarchical_no_prune"])
 def test_runner_up_shortcut_rounds(rf, opts, n, shortcut):
-    """Records held in shared memory (clusters or one CTA) and the register-record kernel select the
-    runner-up as the next sample too when the new sample leaves it unchanged: fewer selection rounds
-    than samples, the oracle's indices all the same.  The hierarchical path (records in global
-    memory; about one point per cell of a uniform cloud) selects one sample a round."""
+    """Every path (records in shared memory on clusters or one CTA, the register-record kernel, the
+    hierarchical path with records in global memory: about one point per cell of a uniform cloud)
+    selects the runner-up as the next sample too when the new sample leaves it unchanged: fewer
+    selection rounds than samples, the oracle's indices all the same."""
     pts = cloudgen.uniform_cloud(n, seed=33) if "n_vox" in opts else cloudgen.room_cloud(n, seed=33)
     m = n * 3 // 20
     o = dict(opts, counters=1)
