@@ -126,18 +126,24 @@ def tune_batch(points: torch.Tensor, sizes, ms, starts=None, candidates=None, re
 def split_candidates(sizes, base_opts):
     """Size splits of a ragged batch to time against its single launch: the k largest clouds (k = 5,
     8, 10) in a launch of their own on 16- or 8-CTA clusters, the rest on 4-CTA clusters or with the
-    single launch's options."""
+    single launch's options.  (Three tiers in one graph measured slower than two: the smallest
+    tier's persistent launch can take every SM before the larger tiers' clusters start.)"""
     order = sorted(sizes, reverse=True)
+    o16 = {"cluster": 16, "threads": 256, "chunk": 128}
+    o8 = {"cluster": 8, "threads": 256, "chunk": 128}
+    o4 = {"cluster": 4, "threads": 256, "chunk": 128}
+
+    def cut(k):   # the size at which the k largest clouds separate from the rest, or None
+        return int(order[k - 1]) if 0 < k < len(order) and order[k] < order[k - 1] else None
+
     cands = []
     for k in (5, 8, 10):
-        if k >= len(order):
+        tail_n = cut(k)
+        if tail_n is None:
             continue
-        tail_n = order[k - 1]
-        if order[k] >= tail_n:   # no clean cut between the k-th and (k+1)-th largest
-            continue
-        for tail_opts in ({"cluster": 16, "threads": 256, "chunk": 128}, {"cluster": 8, "threads": 256, "chunk": 128}):
-            for rest in ({"cluster": 4, "threads": 256, "chunk": 128}, dict(base_opts or {})):
-                cands.append((dict(rest), {"tail_n": int(tail_n), "tail_opts": tail_opts}))
+        for tail_opts in (o16, o8):
+            for rest in (o4, dict(base_opts or {})):
+                cands.append((dict(rest), {"tail_n": tail_n, "tail_opts": tail_opts}))
     return cands
 
 

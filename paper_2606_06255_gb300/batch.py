@@ -10,9 +10,11 @@ graph and replayed, so a step costs one graph launch.
 A ragged batch is bound by the latency of its largest clouds.  With
 split={"tail_n": T, "tail_opts": {...}} the clouds of at least T points form a
 second group, sampled by a launch of its own (for instance on larger clusters)
-that runs beside the first group's on a second stream; both launches, the fork
+that runs beside the first group's on a second stream; split may also be a list
+of such tiers, largest first ([{"tail_n": T1, "tail_opts": ...}, {"tail_n": T2,
+...}]), each cloud going to the first tier it reaches.  All launches, the fork
 and the join are captured in the same graph.  Each group's clouds sit
-contiguously in the point buffer (tail group first), so `rows` gives each
+contiguously in the point buffer (largest tier first), so `rows` gives each
 cloud's rows there; `split()` returns the indices in the caller's cloud order.
 Without a split the sampler also exposes its single launch's `meta`, `offsets`,
 `out_offsets` and `workspace`; with one, each of `groups` holds its own.
@@ -54,15 +56,17 @@ class BatchSampler:
             raise ValueError("1 <= M_b <= N_b for every cloud")
         self.device = torch.device(device if device is not None else "cuda")
         self.opts = opts
-        self.split_spec = dict(split) if split else None
+        tiers = [split] if isinstance(split, dict) else list(split or [])
+        tiers = sorted((dict(t) for t in tiers), key=lambda t: -int(t["tail_n"]))
+        self.split_spec = tiers or None
         b = len(self.sizes)
-        if self.split_spec:
-            tail_n = int(self.split_spec["tail_n"])
-            tail = [i for i in range(b) if self.sizes[i] >= tail_n]
-            rest = [i for i in range(b) if self.sizes[i] < tail_n]
-            plan = [(tail, self.split_spec["tail_opts"]), (rest, opts)]
-        else:
-            plan = [(list(range(b)), opts)]
+        left = list(range(b))
+        plan = []
+        for t in tiers:
+            ids = [i for i in left if self.sizes[i] >= int(t["tail_n"])]
+            left = [i for i in left if self.sizes[i] < int(t["tail_n"])]
+            plan.append((ids, t["tail_opts"]))
+        plan.append((left, opts))
         plan = [(ids, o) for ids, o in plan if ids]
         self.groups = []
         row = out = 0
@@ -87,8 +91,8 @@ class BatchSampler:
             self.offsets = self.meta[3]
             self.out_offsets = self.meta[4]
             self.workspace = self.groups[0].workspace
-        self._side = (torch.cuda.Stream(device=self.device)
-                      if len(self.groups) > 1 and self.device.type == "cuda" else None)
+        self._side = ([torch.cuda.Stream(device=self.device) for _ in self.groups[1:]]
+                      if self.device.type == "cuda" else [])
         self._graph = None
         self.kernels_per_run = None
         if graph:
@@ -105,12 +109,13 @@ class BatchSampler:
 
     def _launch(self, stream=None):
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
-        if len(self.groups) > 1:
-            self._side.wait_stream(s)   # fork before either launch, so that the two run side by side
-        self._launch_group(self.groups[0], s)   # the tail group first: its clusters take SMs first
-        if len(self.groups) > 1:
-            self._launch_group(self.groups[1], self._side)
-            s.wait_stream(self._side)
+        for side in self._side:
+            side.wait_stream(s)   # fork before any launch, so that the groups run side by side
+        self._launch_group(self.groups[0], s)   # the largest tier first: its clusters take SMs first
+        for g, side in zip(self.groups[1:], self._side):
+            self._launch_group(g, side)
+        for side in self._side:
+            s.wait_stream(side)
 
     def _capture(self):
         s = torch.cuda.Stream(device=self.device)

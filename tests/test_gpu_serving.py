@@ -65,17 +65,21 @@ def test_graph_replayed_batch(rf):
         np.testing.assert_array_equal(out3[b], oracle.fps(c, ms[b], 0, threads=0))
 
 
-@pytest.mark.parametrize("tail_opts", [{"cluster": 8, "threads": 256}, {"cluster": 16, "threads": 128, "chunk": 64}])
-def test_graph_replayed_split_batch(rf, tail_opts):
-    """The largest clouds in a concurrent launch of their own (BatchSampler's size split), both
-    launches in one graph: every cloud's indices are the oracle's, in the caller's order, on two
-    replays, and the same as the unsplit batch's."""
+@pytest.mark.parametrize("split", [{"tail_n": 40000, "tail_opts": {"cluster": 8, "threads": 256}},
+                                   {"tail_n": 40000, "tail_opts": {"cluster": 16, "threads": 128, "chunk": 64}},
+                                   [{"tail_n": 50000, "tail_opts": {"cluster": 16, "threads": 256}},
+                                    {"tail_n": 40000, "tail_opts": {"cluster": 8, "threads": 256}}]],
+                         ids=["two_8", "two_16", "three_tiers"])
+def test_graph_replayed_split_batch(rf, split):
+    """The largest clouds in concurrent launches of their own (BatchSampler's size split, in two or
+    three tiers), all launches in one graph: every cloud's indices are the oracle's, in the caller's
+    order, on two replays, and the same as the unsplit batch's."""
     clouds = _mixed(8, 1200) + [cloudgen.lidar_cloud(60000, seed=91), cloudgen.room_cloud(45000, seed=92)]
     sizes = [c.shape[0] for c in clouds]
     ms = [n // 6 for n in sizes]
-    bs = rf.batch.BatchSampler(sizes, ms, opts={"cluster": 2, "threads": 256},
-                               split={"tail_n": 40000, "tail_opts": tail_opts})
-    assert len(bs.groups) == 2 and sorted(bs.groups[0].ids) == [8, 9]
+    bs = rf.batch.BatchSampler(sizes, ms, opts={"cluster": 2, "threads": 256}, split=split)
+    assert len(bs.groups) == (3 if isinstance(split, list) else 2)
+    assert sorted(i for g in bs.groups[:-1] for i in g.ids) == [8, 9]
     bs.load(clouds)
     out1 = bs.split(bs.run().clone())
     out2 = bs.split(bs.run())

@@ -420,6 +420,13 @@ def test_batch_split_layout():
     assert all(hi - lo == n for (lo, hi), n in zip(bs.rows, sizes))
     assert all(hi - lo == m for (lo, hi), m in zip(bs.out_rows, ms))
     assert max(bs.rows[i][1] for i in (1, 3, 4)) <= min(bs.rows[i][0] for i in (0, 2, 5))   # tail group first
+    # three tiers: each cloud in the first tier it reaches, the largest tier first
+    three = batch.BatchSampler(sizes, ms, opts={"cluster": 4}, device="cpu", graph=False,
+                               split=[{"tail_n": 90000, "tail_opts": {"cluster": 8}},
+                                      {"tail_n": 150000, "tail_opts": {"cluster": 16}}])
+    assert [g.ids for g in three.groups] == [[4], [1, 3], [0, 2, 5]]
+    assert [g.opts for g in three.groups] == [{"cluster": 16}, {"cluster": 8}, {"cluster": 4}]
+    assert sorted(three.rows)[-1][1] == sum(sizes) and three.rows[4] == (0, 200000)
     # no split: one group in the caller's order
     one = batch.BatchSampler(sizes, ms, device="cpu", graph=False)
     assert len(one.groups) == 1 and one.rows[0] == (0, 5000) and one.rows[1] == (5000, 125000)
