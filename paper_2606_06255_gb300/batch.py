@@ -91,7 +91,9 @@ class BatchSampler:
             self.offsets = self.meta[3]
             self.out_offsets = self.meta[4]
             self.workspace = self.groups[0].workspace
-        self._side = ([torch.cuda.Stream(device=self.device) for _ in self.groups[1:]]
+        # the smaller tiers run on streams of lower priority, so that the block scheduler starts the
+        # larger tiers' clusters first when both wait for SMs (stream capture records the priority)
+        self._side = ([torch.cuda.Stream(device=self.device, priority=0) for _ in self.groups[1:]]
                       if self.device.type == "cuda" else [])
         self._graph = None
         self.kernels_per_run = None
@@ -118,7 +120,7 @@ class BatchSampler:
             s.wait_stream(side)
 
     def _capture(self):
-        s = torch.cuda.Stream(device=self.device)
+        s = torch.cuda.Stream(device=self.device, priority=-1 if len(self.groups) > 1 else 0)
         s.wait_stream(torch.cuda.current_stream(self.device))
         with torch.cuda.stream(s):
             self._launch(s)          # first call outside capture: kernel attributes, device check
