@@ -126,8 +126,8 @@ def tune_batch(points: torch.Tensor, sizes, ms, starts=None, candidates=None, re
 def split_candidates(sizes, base_opts):
     """Size splits of a ragged batch to time against its single launch: the k largest clouds (k = 5,
     8, 10) in a launch of their own on 16- or 8-CTA clusters, the rest on 4-CTA clusters or with the
-    single launch's options; and three tiers, the k1 largest (3 or 4) on 16-CTA clusters, the next
-    k2 (6 or 8) on 8-CTA clusters, the rest on 4-CTA clusters."""
+    single launch's options.  (Three tiers can be faster, but only when the largest tier's clusters
+    start first, which stream priorities do not guarantee; they are not candidates.)"""
     order = sorted(sizes, reverse=True)
     o16 = {"cluster": 16, "threads": 256, "chunk": 128}
     o8 = {"cluster": 8, "threads": 256, "chunk": 128}
@@ -144,11 +144,6 @@ def split_candidates(sizes, base_opts):
         for tail_opts in (o16, o8):
             for rest in (o4, dict(base_opts or {})):
                 cands.append((dict(rest), {"tail_n": tail_n, "tail_opts": tail_opts}))
-    for k1 in (3, 4):
-        for k2 in (6, 8):
-            t1, t2 = cut(k1), cut(k1 + k2)
-            if t1 is not None and t2 is not None:
-                cands.append((dict(o4), [{"tail_n": t1, "tail_opts": o16}, {"tail_n": t2, "tail_opts": o8}]))
     return cands
 
 
