@@ -430,3 +430,21 @@ def test_batch_split_layout():
     # no split: one group in the caller's order
     one = batch.BatchSampler(sizes, ms, device="cpu", graph=False)
     assert len(one.groups) == 1 and one.rows[0] == (0, 5000) and one.rows[1] == (5000, 125000)
+
+
+def test_batch_split_candidates():
+    """The split tuner's candidates cut the batch between distinct sizes only, keep the k largest
+    clouds in the tail group, and fall back to none for batches too small or too uniform to cut."""
+    from paper_2606_06255_gb300 import autotune
+    sizes = [1000 * (i + 1) for i in range(20)]            # 1k .. 20k, all distinct
+    cands = autotune.split_candidates(sizes, {"cluster": 8})
+    assert len(cands) == 3 * 2 * 2
+    for rest, split in cands:
+        tail = [n for n in sizes if n >= split["tail_n"]]
+        assert len(tail) in (5, 8, 10)
+        assert split["tail_opts"]["cluster"] in (8, 16) and rest["cluster"] in (4, 8)
+    assert autotune.split_candidates([5000] * 20, None) == []          # no size to cut between
+    assert autotune.split_candidates([300, 200, 100], None) == []      # fewer clouds than any k
+    tied = [20] * 4 + [10] * 4 + [5] * 12     # only the 8 largest separate cleanly from the rest
+    got = autotune.split_candidates(tied, None)
+    assert got and {len([n for n in tied if n >= s["tail_n"]]) for _, s in got} == {8}
